@@ -1,0 +1,197 @@
+/*
+ * fe2.h - batched damped dynamic relaxation of many small fiber-network RVEs
+ * on one GB300 GPU (sm_103a).
+ *
+ * Method: Merson & Shephard, "Using Hierarchical Parallelism to Accelerate the
+ * Solution of Many Small Partial Differential Equations". In the FE2 scheme
+ * every macroscale material point solves an independent microscale problem
+ * (Section I); here that problem is a truss (fiber) network relaxed to static
+ * equilibrium by damped explicit central-difference dynamics until the force
+ * residual converges (Algorithm 1, Section III). Many such problems are packed
+ * CRS-style, row offsets plus values, into one batch (the PackedView idea,
+ * Section III) and solved together on the device.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an fe2_status and never aborts or exits.
+ *     fe2_last_error() gives a message for the last failing call of the
+ *     calling thread.
+ *   - Input arrays are caller-owned HOST memory unless a name ends in _dev.
+ *     They are copied before the call returns (or, for the asynchronous _dev
+ *     calls, read on the stream) and may be freed afterwards.
+ *   - Node ids and element connectivity are exactly the caller's. Internal
+ *     reorderings never show in any input or output.
+ *   - 3x3 tensors (F, sigma) are row-major, 9 doubles per RVE.
+ *   - A batch owns all of its device memory until fe2_batch_destroy(). The
+ *     library allocates only in create and destroy; solve allocates nothing.
+ *   - Calls on one batch must not run concurrently from several host threads.
+ */
+#ifndef FE2_H
+#define FE2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe2_batch fe2_batch; /* opaque */
+
+typedef enum {
+    FE2_OK = 0,
+    FE2_EINVAL = 1,   /* invalid argument or input data; nothing changed */
+    FE2_ENOMEM = 2,   /* device or host allocation failed */
+    FE2_ECUDA = 3,    /* a CUDA runtime call failed; see fe2_last_error() */
+    FE2_ESTATE = 4,   /* call out of order (e.g. results before any solve) */
+    FE2_ETIMEOUT = 5, /* a bounded device wait gave up (serving epochs) */
+    FE2_ENODEV = 6    /* no usable sm_103 device */
+} fe2_status;
+
+/* Per-RVE outcome of a solve. */
+typedef enum {
+    FE2_RVE_OK = 0,      /* residual <= tol * f_ref */
+    FE2_RVE_MAXITER = 1, /* max_iter iterations without converging */
+    FE2_RVE_NAN = 2,     /* the residual became NaN or infinite */
+    FE2_RVE_PENDING = 3  /* not solved yet */
+} fe2_rve_status;
+
+typedef enum {
+    /* IEEE FP64 in the order of the reference algorithm: the same operations
+     * in the same order as a serial element-scatter implementation in the
+     * caller's node order, no fused multiply-add, correctly rounded sqrt and
+     * divide. The trajectory is bit for bit that of such an implementation;
+     * only the residual and stress sums are reassociated. */
+    FE2_PREC_FP64 = 0,
+    /* FP32 force and update arithmetic on the FP32 pipes: a double-float lead
+     * phase for the first lead_iters iterations (where the network picks its
+     * equilibrium), then FP32 increments of the element forces about a
+     * double-float reference state that is refreshed every rebase_every
+     * iterations. Residual test and stress sum are FP64. */
+    FE2_PREC_MIXED = 1
+} fe2_precision;
+
+typedef enum {
+    FE2_INIT_REFERENCE = 0, /* free nodes start at u = 0 (only the fixed DOFs move) */
+    FE2_INIT_AFFINE = 1,    /* every node starts at the affine position F X */
+    FE2_INIT_WARM = 2       /* free nodes start at the batch's current displacement
+                               (the last solve's result or fe2_batch_set_displacement) */
+} fe2_init;
+
+typedef struct {
+    double tol;           /* relative residual tolerance, converged when
+                             ||g_free||_2 <= tol * f_ref (default 1e-8) */
+    int64_t max_iter;     /* iteration cap, >= 1 (default 10,000,000) */
+    double dt_safety;     /* time-step safety factor alpha in (0, 1] (default 0.9) */
+    int32_t precision;    /* fe2_precision (default FE2_PREC_MIXED) */
+    int32_t init;         /* fe2_init (default FE2_INIT_AFFINE) */
+    int32_t kinetic_energy; /* 1: also track the kinetic energy 1/2 sum m v^2 */
+    int32_t block_threads;  /* threads per CTA: 0 = default (512, the paper's
+                               team size), else a multiple of 32 in [64, 512] */
+    int64_t lead_iters;   /* MIXED: double-float iterations before the FP32
+                             phase; < 0 = default 1000 (n/512)^(1/3) */
+    int32_t rebase_every; /* MIXED: FP32 iterations between double-float
+                             reference refreshes; <= 0 = default 512 */
+    int32_t reserved;
+} fe2_opts;
+
+/* Fill *opts with the defaults listed above. */
+void fe2_opts_default(fe2_opts *opts);
+
+/*
+ * Create a batch of n_rve networks (Algorithm 1: load mesh, compute edge and
+ * connectivity arrays, transfer them to the device, compute the lumped mass
+ * matrix and the critical time step).
+ *
+ * n_rve     number of RVEs, >= 1.
+ * node_off  n_rve+1 prefix offsets into the node arrays (node_off[0] = 0).
+ * X         3*N reference coordinates, xyz interleaved, N = node_off[n_rve].
+ * elem_off  n_rve+1 prefix offsets into the element arrays.
+ * conn      2*E node ids, LOCAL to the element's RVE (0 .. n_p-1).
+ * EA        E axial rigidities (> 0). The force law is N = EA (l/L - 1).
+ * fixed     N flags: non-zero = prescribed displacement x = F X.
+ * V0        n_rve reference volumes (> 0), or NULL for 1 (unit cube).
+ * damping   n_rve damping coefficients c >= 0 (f_d = -c m v), or NULL for
+ *           c = 0.002 (512 / n_p)^(1/3).
+ * stream    cudaStream_t used for the uploads, or NULL (legacy stream).
+ * out       receives the batch handle.
+ *
+ * Returns FE2_EINVAL if an id is out of range, an element joins a node to
+ * itself or repeats another, a length is zero, EA <= 0, or a value is not
+ * finite. A free node that no element touches is held fixed.
+ */
+fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, const double *X,
+                            const int64_t *elem_off, const int32_t *conn, const double *EA,
+                            const uint8_t *fixed, const double *V0, const double *damping,
+                            void *stream, fe2_batch **out);
+
+/*
+ * Solve every RVE of the batch for its deformation gradient (Algorithm 1,
+ * loop to convergence), asynchronously on `stream`.
+ *
+ * F     9*n_rve doubles, row-major, HOST memory (copied to the device on
+ *       `stream` before the call returns).
+ * opts  solver options, or NULL for fe2_opts_default().
+ *
+ * All RVEs run in one persistent launch per size class; the host returns as
+ * soon as the work is queued. Results are read with fe2_batch_stress() or
+ * fe2_batch_results_dev().
+ */
+fe2_status fe2_batch_solve(fe2_batch *b, const double *F, const fe2_opts *opts, void *stream);
+
+/* As fe2_batch_solve(), with F already in DEVICE memory (9*n_rve doubles). */
+fe2_status fe2_batch_solve_dev(fe2_batch *b, const double *F_dev, const fe2_opts *opts,
+                               void *stream);
+
+/*
+ * Wait for the last solve and copy its results to HOST memory, indexed by RVE.
+ * Any pointer may be NULL.
+ *   sigma    9*n_rve volume-averaged Cauchy stress (1/V) sum_e (N_e/l_e) d_e d_e^T,
+ *            V = det(F) V0, current configuration, row-major
+ *   iters    n_rve iteration counts
+ *   rel_res  n_rve final ||g_free|| / f_ref (0 when f_ref = 0)
+ *   status   n_rve fe2_rve_status values
+ * FE2_ESTATE before the first solve.
+ */
+fe2_status fe2_batch_stress(fe2_batch *b, double *sigma, int64_t *iters, double *rel_res,
+                            int32_t *status);
+
+/* Device-side results of the last solve, copied asynchronously on `stream`
+ * into DEVICE buffers (any may be NULL). Same layouts as fe2_batch_stress(). */
+fe2_status fe2_batch_results_dev(fe2_batch *b, double *sigma_dev, int64_t *iters_dev,
+                                 double *rel_res_dev, int32_t *status_dev, void *stream);
+
+/* Copy the current displacement u = x - X (3*N doubles, caller's node order
+ * and numbering) to HOST memory. Waits for the last solve. */
+fe2_status fe2_batch_get_displacement(fe2_batch *b, double *u);
+
+/* Set the displacement used by the next FE2_INIT_WARM solve (3*N doubles,
+ * HOST memory, caller's numbering). Fixed-node entries are ignored. */
+fe2_status fe2_batch_set_displacement(fe2_batch *b, const double *u);
+
+/* Release every resource of the batch. NULL is accepted. */
+fe2_status fe2_batch_destroy(fe2_batch *b);
+
+/* Batch facts: number of RVEs, total nodes, total elements, and the number
+ * of kernel launches the last solve issued. Any pointer may be NULL. */
+fe2_status fe2_batch_info(const fe2_batch *b, int32_t *n_rve, int64_t *n_nodes,
+                          int64_t *n_elems, int32_t *launches);
+
+/*
+ * The paper's naive path (Section III): the same FP64 algorithm solved one RVE
+ * after another, each iteration as a short sequence of kernel launches
+ * (fused free-DOF vector updates, zeroing plus an atomic scatter of the
+ * element forces, and a residual reduction read back by the host every
+ * iteration to test convergence). Kept as the comparator for the batched
+ * path. Synchronous; results are read with fe2_batch_stress().
+ */
+fe2_status fe2_batch_solve_naive(fe2_batch *b, const double *F, const fe2_opts *opts,
+                                 void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *fe2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE2_H */

@@ -1,0 +1,205 @@
+"""Python binding of the fe2 C ABI (include/fe2.h): argument marshalling only.
+
+Every step of the dynamic-relaxation path runs in the CUDA library
+``libfe2gb300.so`` built from ``csrc/``; this module converts numpy arrays and
+torch tensors to pointers and back. There is no CPU fallback: importing fails
+loudly if the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Batch", "Opts", "last_error", "FE2Error", "LIB_PATH", "RVE_STATUS"]
+
+LIB_PATH = _build.LIB
+RVE_STATUS = {0: "OK", 1: "MAXITER", 2: "NAN", 3: "PENDING"}
+_STATUS = {0: "FE2_OK", 1: "FE2_EINVAL", 2: "FE2_ENOMEM", 3: "FE2_ECUDA", 4: "FE2_ESTATE",
+           5: "FE2_ETIMEOUT", 6: "FE2_ENODEV"}
+
+
+class FE2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("dt_safety", C.c_double),
+                ("precision", C.c_int32), ("init", C.c_int32), ("kinetic_energy", C.c_int32),
+                ("block_threads", C.c_int32), ("lead_iters", C.c_int64),
+                ("rebase_every", C.c_int32), ("reserved", C.c_int32)]
+
+
+def _load():
+    path = LIB_PATH
+    if not os.path.exists(path) or os.environ.get("FE2_REBUILD"):
+        path = _build.build()
+    lib = C.CDLL(path)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    lib.fe2_opts_default.argtypes = [C.POINTER(Opts)]
+    lib.fe2_opts_default.restype = None
+    lib.fe2_batch_create.argtypes = [I32, P, P, P, P, P, P, P, P, P, C.POINTER(P)]
+    lib.fe2_batch_solve.argtypes = [P, P, C.POINTER(Opts), P]
+    lib.fe2_batch_solve_dev.argtypes = [P, P, C.POINTER(Opts), P]
+    lib.fe2_batch_solve_naive.argtypes = [P, P, C.POINTER(Opts), P]
+    lib.fe2_batch_stress.argtypes = [P, P, P, P, P]
+    lib.fe2_batch_results_dev.argtypes = [P, P, P, P, P, P]
+    lib.fe2_batch_get_displacement.argtypes = [P, P]
+    lib.fe2_batch_set_displacement.argtypes = [P, P]
+    lib.fe2_batch_destroy.argtypes = [P]
+    lib.fe2_batch_info.argtypes = [P, P, P, P, P]
+    lib.fe2_last_error.argtypes = []
+    lib.fe2_last_error.restype = C.c_char_p
+    for name in ("fe2_batch_create", "fe2_batch_solve", "fe2_batch_solve_dev",
+                 "fe2_batch_solve_naive", "fe2_batch_stress", "fe2_batch_results_dev",
+                 "fe2_batch_get_displacement", "fe2_batch_set_displacement",
+                 "fe2_batch_destroy", "fe2_batch_info"):
+        getattr(lib, name).restype = C.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def last_error() -> str:
+    return _lib.fe2_last_error().decode()
+
+
+def _check(code):
+    if code != 0:
+        raise FE2Error(code, last_error())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+_PREC = {"fp64": 0, "mixed": 1}
+_INIT = {"reference": 0, "affine": 1, "warm": 2}
+
+
+def make_opts(tol=1e-8, max_iter=10_000_000, dt_safety=0.9, precision="mixed", init="affine",
+              kinetic_energy=False, block_threads=0, lead_iters=-1, rebase_every=0) -> Opts:
+    o = Opts()
+    _lib.fe2_opts_default(C.byref(o))
+    o.tol = float(tol)
+    o.max_iter = int(max_iter)
+    o.dt_safety = float(dt_safety)
+    o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    o.init = _INIT[init] if isinstance(init, str) else int(init)
+    o.kinetic_energy = int(bool(kinetic_energy))
+    o.block_threads = int(block_threads)
+    o.lead_iters = int(lead_iters)
+    o.rebase_every = int(rebase_every)
+    return o
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+class Batch:
+    """A packed batch of RVEs resident on the current CUDA device.
+
+    ``nets`` is a list of objects with ``X (n,3)``, ``elems (E,2)``, ``EA (E,)``,
+    ``fixed (n,)`` and ``V0`` (e.g. ``rve_inputs.Network``).
+    """
+
+    def __init__(self, nets, damping=None, stream=None):
+        n_rve = len(nets)
+        node_off = np.zeros(n_rve + 1, np.int64)
+        elem_off = np.zeros(n_rve + 1, np.int64)
+        for p, net in enumerate(nets):
+            node_off[p + 1] = node_off[p] + net.X.shape[0]
+            elem_off[p + 1] = elem_off[p] + net.elems.shape[0]
+        X = np.ascontiguousarray(np.concatenate([n.X for n in nets]), np.float64)
+        conn = np.ascontiguousarray(np.concatenate([n.elems for n in nets]), np.int32)
+        EA = np.ascontiguousarray(np.concatenate([n.EA for n in nets]), np.float64)
+        fixed = np.ascontiguousarray(np.concatenate([n.fixed for n in nets]), np.uint8)
+        V0 = np.ascontiguousarray([getattr(n, "V0", 1.0) for n in nets], np.float64)
+        damp = None if damping is None else np.ascontiguousarray(damping, np.float64)
+        h = C.c_void_p()
+        _check(_lib.fe2_batch_create(n_rve, _ptr(node_off), _ptr(X), _ptr(elem_off), _ptr(conn),
+                                     _ptr(EA), _ptr(fixed), _ptr(V0), _ptr(damp),
+                                     _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self.n_rve = n_rve
+        self.n_nodes = int(node_off[-1])
+        self.node_off = node_off
+
+    # -- solves ---------------------------------------------------------------
+    def solve(self, F, stream=None, **opts):
+        """Queue a solve for host F (P,3,3); returns immediately."""
+        Fh = np.ascontiguousarray(F, np.float64).reshape(self.n_rve, 9)
+        o = make_opts(**opts)
+        _check(_lib.fe2_batch_solve(self._h, _ptr(Fh), C.byref(o), _stream_handle(stream)))
+
+    def solve_dev(self, F_dev, stream=None, **opts):
+        """Queue a solve for F already on the device (a CUDA tensor of 9*P doubles)."""
+        o = make_opts(**opts)
+        _check(_lib.fe2_batch_solve_dev(self._h, C.c_void_p(F_dev.data_ptr()), C.byref(o),
+                                        _stream_handle(stream)))
+
+    def solve_naive(self, F, stream=None, **opts):
+        """The paper's naive per-RVE launch loop (FP64, synchronous)."""
+        Fh = np.ascontiguousarray(F, np.float64).reshape(self.n_rve, 9)
+        o = make_opts(**opts)
+        _check(_lib.fe2_batch_solve_naive(self._h, _ptr(Fh), C.byref(o), _stream_handle(stream)))
+
+    # -- results --------------------------------------------------------------
+    def stress(self):
+        P = self.n_rve
+        sig = np.zeros((P, 9))
+        it = np.zeros(P, np.int64)
+        rr = np.zeros(P)
+        st = np.zeros(P, np.int32)
+        _check(_lib.fe2_batch_stress(self._h, _ptr(sig), _ptr(it), _ptr(rr), _ptr(st)))
+        return {"sigma": sig.reshape(P, 3, 3), "iters": it, "rel_res": rr,
+                "status": [RVE_STATUS[int(s)] for s in st]}
+
+    def results_dev(self, sigma_dev=None, iters_dev=None, rel_dev=None, status_dev=None,
+                    stream=None):
+        def dp(t):
+            return None if t is None else C.c_void_p(t.data_ptr())
+        _check(_lib.fe2_batch_results_dev(self._h, dp(sigma_dev), dp(iters_dev), dp(rel_dev),
+                                          dp(status_dev), _stream_handle(stream)))
+
+    def displacement(self):
+        u = np.zeros((self.n_nodes, 3))
+        _check(_lib.fe2_batch_get_displacement(self._h, _ptr(u)))
+        return u
+
+    def set_displacement(self, u):
+        uh = np.ascontiguousarray(u, np.float64).reshape(self.n_nodes, 3)
+        _check(_lib.fe2_batch_set_displacement(self._h, _ptr(uh)))
+
+    def info(self):
+        a, b, c, d = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+        _check(_lib.fe2_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return {"n_rve": a.value, "n_nodes": b.value, "n_elems": c.value, "launches": d.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(_lib.fe2_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,683 @@
+// Host runtime behind the C ABI of include/fe2.h: input validation, packing
+// into the device layout of fe2_internal.h, size classes, the cost-ordered work
+// queue, persistent launches, and result readback.
+//
+// Algorithm 1 steps 1-3 (load mesh, build connectivity, transfer to the GPU)
+// happen here once per batch; steps 4 onward run in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/fe2.h"
+#include "fe2_internal.h"
+
+using namespace fe2;
+
+namespace {
+
+thread_local std::string g_err;
+
+fe2_status fail(fe2_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? FE2_ENOMEM : FE2_ECUDA,          \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count) {
+        n = count;
+        if (count == 0) return cudaSuccess;
+        return cudaMalloc(&p, sizeof(T) * count);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+// One size class: RVEs solved by one persistent launch.
+struct SizeClass {
+    int smem_positions;       // positions in shared memory
+    size_t smem_bytes;        // dynamic shared memory per CTA
+    std::vector<int32_t> rves;  // in scheduling order
+    int32_t queue_off;        // offset of its queue in the device queue buffer
+};
+
+}  // namespace
+
+struct fe2_batch {
+    int32_t n_rve = 0;
+    int64_t n_nodes = 0, n_elems = 0, n_csr = 0;
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    std::vector<RveDesc> rve;             // host copy
+    std::vector<int64_t> perm_to_orig;    // permuted global -> caller global node
+    std::vector<int32_t> n_nodes_of;      // per RVE
+    std::vector<uint8_t> is_fixed_perm;   // permuted
+
+    // device arrays
+    DevBuf<RveDesc> d_rve;
+    DevBuf<double> d_X, d_mass, d_EA_csr, d_L_csr, d_el_EA, d_el_L;
+    DevBuf<float> d_inv_mass_f;
+    DevBuf<int32_t> d_rowptr, d_col, d_el_a, d_el_b;
+    DevBuf<float2> d_eaf;
+    DevBuf<double> d_u, d_v, d_a, d_xg;
+    DevBuf<float> d_fv, d_fa, d_fg;
+    DevBuf<float4> d_pg;
+    DevBuf<double> d_F, d_sigma, d_rel, d_fref, d_ke;
+    DevBuf<int64_t> d_iters;
+    DevBuf<int32_t> d_status, d_queue, d_counters;
+
+    std::vector<SizeClass> classes_fp64, classes_mixed;
+    bool solved = false;
+    int32_t last_launches = 0;
+    cudaStream_t last_stream = nullptr;
+    std::vector<cudaStream_t> side;  // forked streams for concurrent classes
+    std::vector<cudaEvent_t> ev;
+    DevBuf<double> d_naive;           // naive comparator scratch (allocated on first use)
+    double *h_F = nullptr;             // pinned staging for F
+    cudaEvent_t ev_F = nullptr;        // completion of the last F upload
+
+    DevMesh mesh() const {
+        DevMesh m;
+        m.rve = d_rve.p;
+        m.X0 = d_X.p;
+        m.X1 = d_X.p + n_nodes;
+        m.X2 = d_X.p + 2 * n_nodes;
+        m.mass = d_mass.p;
+        m.inv_mass_f = d_inv_mass_f.p;
+        m.rowptr = d_rowptr.p;
+        m.col = d_col.p;
+        m.EA = d_EA_csr.p;
+        m.L = d_L_csr.p;
+        m.EAf_invLf = d_eaf.p;
+        m.el_a = d_el_a.p;
+        m.el_b = d_el_b.p;
+        m.el_EA = d_el_EA.p;
+        m.el_L = d_el_L.p;
+        return m;
+    }
+    DevState state() const {
+        DevState s;
+        s.u0 = d_u.p; s.u1 = d_u.p + n_nodes; s.u2 = d_u.p + 2 * n_nodes;
+        s.v0 = d_v.p; s.v1 = d_v.p + n_nodes; s.v2 = d_v.p + 2 * n_nodes;
+        s.a0 = d_a.p; s.a1 = d_a.p + n_nodes; s.a2 = d_a.p + 2 * n_nodes;
+        s.fv = d_fv.p; s.fa = d_fa.p; s.fg = d_fg.p;
+        s.xg = d_xg.p;
+        s.pg = d_pg.p;
+        return s;
+    }
+    DevResults results() const {
+        DevResults r;
+        r.sigma = d_sigma.p; r.iters = d_iters.p; r.rel_res = d_rel.p;
+        r.status = d_status.p; r.f_ref = d_fref.p; r.ke = d_ke.p;
+        return r;
+    }
+    void release() {
+        d_rve.release(); d_X.release(); d_mass.release(); d_EA_csr.release(); d_L_csr.release();
+        d_el_EA.release(); d_el_L.release(); d_inv_mass_f.release(); d_rowptr.release();
+        d_col.release(); d_el_a.release(); d_el_b.release(); d_eaf.release(); d_u.release();
+        d_v.release(); d_a.release(); d_xg.release(); d_fv.release(); d_fa.release();
+        d_fg.release(); d_pg.release(); d_F.release(); d_sigma.release(); d_rel.release();
+        d_fref.release(); d_ke.release(); d_iters.release(); d_status.release();
+        d_queue.release(); d_counters.release(); d_naive.release();
+        if (h_F) cudaFreeHost(h_F);
+        h_F = nullptr;
+        if (ev_F) cudaEventDestroy(ev_F);
+        ev_F = nullptr;
+        for (auto s : side) cudaStreamDestroy(s);
+        for (auto e : ev) cudaEventDestroy(e);
+        side.clear();
+        ev.clear();
+    }
+};
+
+extern "C" {
+
+void fe2_opts_default(fe2_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-8;
+    o->max_iter = 10000000;
+    o->dt_safety = 0.9;
+    o->precision = FE2_PREC_MIXED;
+    o->init = FE2_INIT_AFFINE;
+    o->kinetic_energy = 0;
+    o->block_threads = 0;
+    o->lead_iters = -1;
+    o->rebase_every = 0;
+}
+
+const char *fe2_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
+
+namespace {
+
+bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+// Shared-memory bytes a CTA needs to stage one RVE's positions.
+size_t smem_need(int precision, int n) {
+    return precision == FE2_PREC_FP64 ? (size_t)24 * n : (size_t)32 * n;
+}
+
+// Bucket RVEs into classes by staged footprint so that small RVEs are not
+// limited by the occupancy of the largest; too-large RVEs stage in L2 scratch.
+void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
+    out.clear();
+    const size_t cap = b->smem_optin - 1024;  // leave room for static shared memory
+    const size_t bounds[] = {16u << 10, 32u << 10, 56u << 10, 112u << 10, cap};
+    std::vector<SizeClass> cls(6);
+    for (int c = 0; c < 5; ++c) { cls[c].smem_positions = 1; cls[c].smem_bytes = 0; }
+    cls[5].smem_positions = 0;
+    cls[5].smem_bytes = 0;
+    // cost-ordered (largest first): longest-processing-time scheduling
+    std::vector<int32_t> order(b->n_rve);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return b->rve[x].n_free > b->rve[y].n_free;
+    });
+    for (int32_t p : order) {
+        const size_t need = smem_need(precision, b->rve[p].n_nodes);
+        int c = 5;
+        for (int k = 0; k < 5; ++k)
+            if (need <= bounds[k] && need <= cap) { c = k; break; }
+        cls[c].rves.push_back(p);
+        if (c < 5) cls[c].smem_bytes = std::max(cls[c].smem_bytes, need);
+    }
+    int32_t off = 0;
+    for (auto &c : cls) {
+        if (c.rves.empty()) continue;
+        c.queue_off = off;
+        off += (int32_t)c.rves.size();
+        out.push_back(c);
+    }
+}
+
+}  // namespace
+
+extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, const double *X,
+                                       const int64_t *elem_off, const int32_t *conn,
+                                       const double *EA, const uint8_t *fixed, const double *V0,
+                                       const double *damping, void *stream, fe2_batch **out) {
+    if (!out) return fail(FE2_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_rve < 1) return fail(FE2_EINVAL, "n_rve must be >= 1");
+    if (!node_off || !X || !elem_off || !fixed) return fail(FE2_EINVAL, "NULL input array");
+    if (node_off[0] != 0 || elem_off[0] != 0) return fail(FE2_EINVAL, "offsets must start at 0");
+    for (int32_t p = 0; p < n_rve; ++p) {
+        if (node_off[p + 1] <= node_off[p]) return fail(FE2_EINVAL, "RVE " + std::to_string(p) + " has no nodes");
+        if (node_off[p + 1] - node_off[p] > (1 << 30)) return fail(FE2_EINVAL, "RVE too large");
+        if (elem_off[p + 1] < elem_off[p]) return fail(FE2_EINVAL, "element offsets decrease");
+    }
+    const int64_t N = node_off[n_rve], E = elem_off[n_rve];
+    if (E > 0 && (!conn || !EA)) return fail(FE2_EINVAL, "NULL conn or EA");
+
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(FE2_ENODEV, std::string("need an sm_103 GPU, found ") + prop.name);
+
+    // ---- validation ----
+    for (int64_t i = 0; i < N; ++i)
+        if (!finite3(X + 3 * i)) return fail(FE2_EINVAL, "non-finite coordinate at node " + std::to_string(i));
+    for (int32_t p = 0; p < n_rve; ++p) {
+        if (V0 && !(V0[p] > 0.0 && std::isfinite(V0[p]))) return fail(FE2_EINVAL, "V0 must be > 0");
+        if (damping && !(damping[p] >= 0.0 && std::isfinite(damping[p])))
+            return fail(FE2_EINVAL, "damping must be finite and >= 0");
+        const int64_t np_ = node_off[p + 1] - node_off[p];
+        std::vector<std::pair<int64_t, int64_t>> keys;
+        keys.reserve(elem_off[p + 1] - elem_off[p]);
+        for (int64_t e = elem_off[p]; e < elem_off[p + 1]; ++e) {
+            const int64_t a = conn[2 * e], c = conn[2 * e + 1];
+            if (a < 0 || c < 0 || a >= np_ || c >= np_)
+                return fail(FE2_EINVAL, "element " + std::to_string(e) + ": node id out of range");
+            if (a == c) return fail(FE2_EINVAL, "element " + std::to_string(e) + " joins a node to itself");
+            if (!(EA[e] > 0.0 && std::isfinite(EA[e])))
+                return fail(FE2_EINVAL, "element " + std::to_string(e) + ": EA must be finite and > 0");
+            const double *xa = X + 3 * (node_off[p] + a), *xb = X + 3 * (node_off[p] + c);
+            if (xa[0] == xb[0] && xa[1] == xb[1] && xa[2] == xb[2])
+                return fail(FE2_EINVAL, "element " + std::to_string(e) + " has zero length");
+            keys.emplace_back(std::min(a, c), std::max(a, c));
+        }
+        std::sort(keys.begin(), keys.end());
+        if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
+            return fail(FE2_EINVAL, "RVE " + std::to_string(p) + " repeats an element");
+    }
+
+    fe2_batch *b = new fe2_batch();
+    b->n_rve = n_rve;
+    b->n_nodes = N;
+    b->n_elems = E;
+    b->n_csr = 2 * E;
+    b->device = dev;
+    b->sm_count = prop.multiProcessorCount;
+    b->smem_optin = prop.sharedMemPerBlockOptin;
+    b->rve.resize(n_rve);
+    b->perm_to_orig.resize(N);
+    b->n_nodes_of.resize(n_rve);
+    b->is_fixed_perm.resize(N);
+
+    // ---- packing: permutation, CSR rows, element list ----
+    std::vector<double> hX(3 * N);
+    std::vector<double> hEAcsr(2 * E), hElEA(E);
+    std::vector<int32_t> hcol(2 * E), hEla(E), hElb(E);
+    std::vector<int64_t> hElemOf(2 * E), hGa(E), hGb(E);
+    std::vector<int32_t> hrow((size_t)N + n_rve);
+    int64_t csr_pos = 0;
+    for (int32_t p = 0; p < n_rve; ++p) {
+        const int64_t base = node_off[p];
+        const int n = (int)(node_off[p + 1] - base);
+        const int64_t e0 = elem_off[p], ne = elem_off[p + 1] - e0;
+        std::vector<int> deg(n, 0);
+        for (int64_t e = e0; e < e0 + ne; ++e) { deg[conn[2 * e]]++; deg[conn[2 * e + 1]]++; }
+        std::vector<uint8_t> fx(n);
+        for (int i = 0; i < n; ++i) fx[i] = (fixed[base + i] != 0) || deg[i] == 0;
+        // free nodes first, by degree (descending), then fixed nodes; stable by id
+        std::vector<int> order(n);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            if (fx[x] != fx[y]) return fx[x] < fx[y];
+            if (!fx[x]) return deg[x] > deg[y];
+            return false;
+        });
+        std::vector<int> newid(n);
+        int nfree = 0, maxdeg = 0;
+        for (int k = 0; k < n; ++k) {
+            newid[order[k]] = k;
+            if (!fx[order[k]]) ++nfree;
+            maxdeg = std::max(maxdeg, deg[order[k]]);
+        }
+        // CSR rows in permuted order, entries sorted by ORIGINAL neighbour id.
+        std::vector<std::vector<std::pair<int, int64_t>>> rows(n);
+        for (int64_t e = e0; e < e0 + ne; ++e) {
+            const int a = conn[2 * e], c = conn[2 * e + 1];
+            rows[a].push_back({c, e});
+            rows[c].push_back({a, e});
+        }
+        RveDesc &R = b->rve[p];
+        R.node0 = base;
+        R.rp0 = base + p;
+        R.csr0 = csr_pos;
+        R.elem0 = e0;
+        R.n_nodes = n;
+        R.n_free = nfree;
+        R.n_elems = (int32_t)ne;
+        R.max_deg = maxdeg;
+        R.dtc = 0.0;
+        R.c = damping ? damping[p] : 0.002 * std::cbrt(512.0 / (double)n);
+        R.V0 = V0 ? V0[p] : 1.0;
+        R.pad = 0.0;
+        b->n_nodes_of[p] = n;
+        int32_t local = 0;
+        for (int k = 0; k < n; ++k) {
+            const int orig = order[k];
+            b->perm_to_orig[base + k] = base + orig;
+            b->is_fixed_perm[base + k] = fx[orig];
+            for (int r = 0; r < 3; ++r) hX[r * N + base + k] = X[3 * (base + orig) + r];
+            auto &row = rows[orig];
+            std::sort(row.begin(), row.end());
+            hrow[R.rp0 + k] = local;
+            for (auto &pr : row) {
+                hcol[csr_pos + local] = newid[pr.first];
+                hElemOf[csr_pos + local] = pr.second;
+                hEAcsr[csr_pos + local] = EA[pr.second];
+                ++local;
+            }
+        }
+        hrow[R.rp0 + n] = local;
+        csr_pos += local;
+        for (int64_t e = e0; e < e0 + ne; ++e) {
+            // keep the caller's orientation (a, b) for the stress sum
+            hEla[e] = newid[conn[2 * e]];
+            hElb[e] = newid[conn[2 * e + 1]];
+            hGa[e] = base + newid[conn[2 * e]];
+            hGb[e] = base + newid[conn[2 * e + 1]];
+            hElEA[e] = EA[e];
+        }
+    }
+    // The oracle-order guarantee needs a < b in the caller's numbering for the
+    // length orientation only through squares, which are symmetric; the stress
+    // uses the caller's (a, b) as given.
+
+    // ---- device allocation and upload ----
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fe2_status rc = FE2_OK;
+    auto A = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && rc == FE2_OK) {
+            rc = e == cudaErrorMemoryAllocation ? FE2_ENOMEM : FE2_ECUDA;
+            g_err = std::string(what) + ": " + cudaGetErrorString(e);
+        }
+    };
+    DevBuf<int64_t> d_elemof, d_ga, d_gb;
+    A(b->d_rve.alloc(n_rve), "rve");
+    A(b->d_X.alloc(3 * N), "X");
+    A(b->d_mass.alloc(N), "mass");
+    A(b->d_inv_mass_f.alloc(N), "inv_mass");
+    A(b->d_EA_csr.alloc(2 * E), "EA_csr");
+    A(b->d_L_csr.alloc(2 * E), "L_csr");
+    A(b->d_eaf.alloc(2 * E), "eaf");
+    A(b->d_col.alloc(2 * E), "col");
+    A(b->d_rowptr.alloc(N + n_rve), "rowptr");
+    A(b->d_el_a.alloc(E), "el_a");
+    A(b->d_el_b.alloc(E), "el_b");
+    A(b->d_el_EA.alloc(E), "el_EA");
+    A(b->d_el_L.alloc(E), "el_L");
+    A(b->d_u.alloc(3 * N), "u");
+    A(b->d_v.alloc(3 * N), "v");
+    A(b->d_a.alloc(3 * N), "a");
+    A(b->d_F.alloc(9 * (size_t)n_rve), "F");
+    A(b->d_sigma.alloc(9 * (size_t)n_rve), "sigma");
+    A(b->d_rel.alloc(n_rve), "rel");
+    A(b->d_fref.alloc(n_rve), "fref");
+    A(b->d_ke.alloc(n_rve), "ke");
+    A(b->d_iters.alloc(n_rve), "iters");
+    A(b->d_status.alloc(n_rve), "status");
+    A(b->d_queue.alloc(2 * (size_t)n_rve), "queue");
+    A(b->d_counters.alloc(32), "counters");
+    A(d_elemof.alloc(2 * E), "elemof");
+    A(d_ga.alloc(E), "ga");
+    A(d_gb.alloc(E), "gb");
+    if (rc != FE2_OK) {
+        d_elemof.release(); d_ga.release(); d_gb.release();
+        b->release();
+        delete b;
+        return rc;
+    }
+    auto H2D = [&](void *dst, const void *src, size_t bytes, const char *what) {
+        if (bytes) A(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), what);
+    };
+    H2D(b->d_rve.p, b->rve.data(), sizeof(RveDesc) * n_rve, "rve");
+    H2D(b->d_X.p, hX.data(), sizeof(double) * 3 * N, "X");
+    H2D(b->d_EA_csr.p, hEAcsr.data(), sizeof(double) * 2 * E, "EA_csr");
+    H2D(b->d_col.p, hcol.data(), sizeof(int32_t) * 2 * E, "col");
+    H2D(b->d_rowptr.p, hrow.data(), sizeof(int32_t) * (N + n_rve), "rowptr");
+    H2D(b->d_el_a.p, hEla.data(), sizeof(int32_t) * E, "el_a");
+    H2D(b->d_el_b.p, hElb.data(), sizeof(int32_t) * E, "el_b");
+    H2D(b->d_el_EA.p, hElEA.data(), sizeof(double) * E, "el_EA");
+    H2D(d_elemof.p, hElemOf.data(), sizeof(int64_t) * 2 * E, "elemof");
+    H2D(d_ga.p, hGa.data(), sizeof(int64_t) * E, "ga");
+    H2D(d_gb.p, hGb.data(), sizeof(int64_t) * E, "gb");
+    if (rc == FE2_OK) A(cudaMemsetAsync(b->d_u.p, 0, sizeof(double) * 3 * N, st), "u zero");
+    if (rc == FE2_OK) {
+        int e = launch_setup(n_rve, E, 2 * E, b->d_rve.p, d_ga.p, d_gb.p, b->d_X.p, b->d_X.p + N,
+                             b->d_X.p + 2 * N, d_elemof.p, b->d_EA_csr.p, b->d_el_EA.p,
+                             b->d_rowptr.p, b->d_el_L.p, b->d_L_csr.p, b->d_eaf.p, b->d_mass.p,
+                             b->d_inv_mass_f.p, st);
+        A((cudaError_t)e, "setup kernels");
+    }
+    if (rc == FE2_OK) A(cudaMemcpyAsync(b->rve.data(), b->d_rve.p, sizeof(RveDesc) * n_rve,
+                                        cudaMemcpyDeviceToHost, st), "rve readback");
+    if (rc == FE2_OK) A(cudaStreamSynchronize(st), "create sync");
+    d_elemof.release(); d_ga.release(); d_gb.release();
+    if (rc != FE2_OK) {
+        b->release();
+        delete b;
+        return rc;
+    }
+    build_classes(b, FE2_PREC_FP64, b->classes_fp64);
+    build_classes(b, FE2_PREC_MIXED, b->classes_mixed);
+    {
+        // work queues: per class, RVE ids in scheduling order (FP64, then mixed)
+        std::vector<int32_t> q(2 * (size_t)n_rve);
+        for (auto &c : b->classes_fp64) std::copy(c.rves.begin(), c.rves.end(), q.begin() + c.queue_off);
+        for (auto &c : b->classes_mixed)
+            std::copy(c.rves.begin(), c.rves.end(), q.begin() + n_rve + c.queue_off);
+        A(cudaMemcpy(b->d_queue.p, q.data(), sizeof(int32_t) * 2 * n_rve, cudaMemcpyHostToDevice),
+          "queue");
+        A(cudaMallocHost(&b->h_F, sizeof(double) * 9 * n_rve), "pinned F");
+        A(cudaEventCreateWithFlags(&b->ev_F, cudaEventDisableTiming), "F event");
+    }
+    // scratch for RVEs that stage positions in L2 instead of shared memory
+    bool need_xg = false, need_pg = false;
+    for (auto &c : b->classes_fp64) need_xg |= !c.smem_positions;
+    for (auto &c : b->classes_mixed) need_pg |= !c.smem_positions;
+    if (need_xg) A(b->d_xg.alloc(3 * N), "xg");
+    if (need_pg) A(b->d_pg.alloc(2 * N), "pg");
+    A(b->d_fv.alloc(3 * N), "fv");
+    A(b->d_fa.alloc(3 * N), "fa");
+    A(b->d_fg.alloc(3 * N), "fg");
+    for (int k = 0; k < 6 && rc == FE2_OK; ++k) {
+        cudaStream_t s;
+        A(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+        if (rc == FE2_OK) b->side.push_back(s);
+    }
+    for (int k = 0; k < 8 && rc == FE2_OK; ++k) {
+        cudaEvent_t e;
+        A(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        if (rc == FE2_OK) b->ev.push_back(e);
+    }
+    if (rc != FE2_OK) {
+        b->release();
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return FE2_OK;
+}
+
+namespace {
+
+fe2_status check_opts(const fe2_opts &o) {
+    if (!(o.tol >= 0.0) || !std::isfinite(o.tol)) return fail(FE2_EINVAL, "tol must be finite and >= 0");
+    if (o.max_iter < 1) return fail(FE2_EINVAL, "max_iter must be >= 1");
+    if (!(o.dt_safety > 0.0 && o.dt_safety <= 1.0)) return fail(FE2_EINVAL, "dt_safety must be in (0, 1]");
+    if (o.precision != FE2_PREC_FP64 && o.precision != FE2_PREC_MIXED)
+        return fail(FE2_EINVAL, "unknown precision");
+    if (o.init < 0 || o.init > 2) return fail(FE2_EINVAL, "unknown init");
+    if (o.block_threads != 0 && (o.block_threads < 64 || o.block_threads > 512 || o.block_threads % 32))
+        return fail(FE2_EINVAL, "block_threads must be 0 or a multiple of 32 in [64, 512]");
+    return FE2_OK;
+}
+
+fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
+    const bool fp64 = o.precision == FE2_PREC_FP64;
+    auto &classes = fp64 ? b->classes_fp64 : b->classes_mixed;
+    CUDA_TRY(cudaMemsetAsync(b->d_counters.p, 0, sizeof(int32_t) * 32, st));
+    const int block = o.block_threads ? o.block_threads : 512;
+    SolveParams P;
+    P.F = b->d_F.p;
+    P.tol = o.tol;
+    P.max_iter = o.max_iter;
+    P.alpha = o.dt_safety;
+    P.init = o.init;
+    P.want_ke = o.kinetic_energy;
+    P.lead_iters = o.lead_iters;
+    P.rebase_every = o.rebase_every;
+    const DevMesh M = b->mesh();
+    const DevState S = b->state();
+    const DevResults R = b->results();
+    // fork: every class runs on its own stream, concurrently
+    CUDA_TRY(cudaEventRecord(b->ev[0], st));
+    int launches = 0;
+    for (size_t k = 0; k < classes.size(); ++k) {
+        const SizeClass &c = classes[k];
+        cudaStream_t s = b->side[k];
+        CUDA_TRY(cudaStreamWaitEvent(s, b->ev[0], 0));
+        P.queue = b->d_queue.p + (fp64 ? 0 : b->n_rve) + c.queue_off;
+        P.queue_len = (int32_t)c.rves.size();
+        P.counter = b->d_counters.p + k;
+        P.smem_positions = c.smem_positions;
+        const size_t smem = c.smem_positions ? c.smem_bytes : 0;
+        int per_sm = fp64 ? occupancy_dr_fp64(c.smem_positions, block, smem)
+                          : occupancy_dr_mixed(c.smem_positions, block, smem);
+        per_sm = std::max(1, per_sm);
+        const int grid = std::max(1, std::min<int>((int)c.rves.size(), per_sm * b->sm_count));
+        const int e = fp64 ? launch_dr_fp64(M, S, R, P, grid, block, smem, s)
+                           : launch_dr_mixed(M, S, R, P, grid, block, smem, s);
+        if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
+        ++launches;
+        CUDA_TRY(cudaEventRecord(b->ev[1 + k], s));
+        CUDA_TRY(cudaStreamWaitEvent(st, b->ev[1 + k], 0));
+    }
+    b->last_launches = launches;
+    b->last_stream = st;
+    b->solved = true;
+    return FE2_OK;
+}
+
+}  // namespace
+
+extern "C" fe2_status fe2_batch_solve_dev(fe2_batch *b, const double *F_dev, const fe2_opts *opts,
+                                          void *stream) {
+    if (!b || !F_dev) return fail(FE2_EINVAL, "NULL batch or F");
+    fe2_opts o;
+    if (opts) o = *opts; else fe2_opts_default(&o);
+    fe2_status s = check_opts(o);
+    if (s != FE2_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemcpyAsync(b->d_F.p, F_dev, sizeof(double) * 9 * b->n_rve,
+                             cudaMemcpyDeviceToDevice, st));
+    return launch_solve(b, o, st);
+}
+
+extern "C" fe2_status fe2_batch_solve(fe2_batch *b, const double *F, const fe2_opts *opts,
+                                      void *stream) {
+    if (!b || !F) return fail(FE2_EINVAL, "NULL batch or F");
+    fe2_opts o;
+    if (opts) o = *opts; else fe2_opts_default(&o);
+    fe2_status s = check_opts(o);
+    if (s != FE2_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Stage F in pinned memory so the caller's buffer is free on return; the
+    // previous solve's upload from the staging buffer must have completed.
+    CUDA_TRY(cudaEventSynchronize(b->ev_F));
+    std::memcpy(b->h_F, F, sizeof(double) * 9 * b->n_rve);
+    CUDA_TRY(cudaMemcpyAsync(b->d_F.p, b->h_F, sizeof(double) * 9 * b->n_rve, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaEventRecord(b->ev_F, st));
+    return launch_solve(b, o, st);
+}
+
+extern "C" fe2_status fe2_batch_stress(fe2_batch *b, double *sigma, int64_t *iters, double *rel_res,
+                                       int32_t *status) {
+    if (!b) return fail(FE2_EINVAL, "NULL batch");
+    if (!b->solved) return fail(FE2_ESTATE, "no solve has been issued");
+    CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    const size_t P = b->n_rve;
+    if (sigma) CUDA_TRY(cudaMemcpy(sigma, b->d_sigma.p, sizeof(double) * 9 * P, cudaMemcpyDeviceToHost));
+    if (iters) CUDA_TRY(cudaMemcpy(iters, b->d_iters.p, sizeof(int64_t) * P, cudaMemcpyDeviceToHost));
+    if (rel_res) CUDA_TRY(cudaMemcpy(rel_res, b->d_rel.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    if (status) CUDA_TRY(cudaMemcpy(status, b->d_status.p, sizeof(int32_t) * P, cudaMemcpyDeviceToHost));
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_results_dev(fe2_batch *b, double *sigma_dev, int64_t *iters_dev,
+                                            double *rel_res_dev, int32_t *status_dev, void *stream) {
+    if (!b) return fail(FE2_EINVAL, "NULL batch");
+    if (!b->solved) return fail(FE2_ESTATE, "no solve has been issued");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t P = b->n_rve;
+    if (sigma_dev) CUDA_TRY(cudaMemcpyAsync(sigma_dev, b->d_sigma.p, sizeof(double) * 9 * P, cudaMemcpyDeviceToDevice, st));
+    if (iters_dev) CUDA_TRY(cudaMemcpyAsync(iters_dev, b->d_iters.p, sizeof(int64_t) * P, cudaMemcpyDeviceToDevice, st));
+    if (rel_res_dev) CUDA_TRY(cudaMemcpyAsync(rel_res_dev, b->d_rel.p, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
+    if (status_dev) CUDA_TRY(cudaMemcpyAsync(status_dev, b->d_status.p, sizeof(int32_t) * P, cudaMemcpyDeviceToDevice, st));
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_get_displacement(fe2_batch *b, double *u) {
+    if (!b || !u) return fail(FE2_EINVAL, "NULL batch or u");
+    if (b->solved) CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    const int64_t N = b->n_nodes;
+    std::vector<double> h(3 * N);
+    CUDA_TRY(cudaMemcpy(h.data(), b->d_u.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < N; ++k) {
+        const int64_t o = b->perm_to_orig[k];
+        for (int r = 0; r < 3; ++r) u[3 * o + r] = h[r * N + k];
+    }
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_set_displacement(fe2_batch *b, const double *u) {
+    if (!b || !u) return fail(FE2_EINVAL, "NULL batch or u");
+    const int64_t N = b->n_nodes;
+    for (int64_t k = 0; k < 3 * N; ++k)
+        if (!std::isfinite(u[k])) return fail(FE2_EINVAL, "non-finite displacement");
+    if (b->solved) CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    std::vector<double> h(3 * N);
+    for (int64_t k = 0; k < N; ++k) {
+        const int64_t o = b->perm_to_orig[k];
+        for (int r = 0; r < 3; ++r) h[r * N + k] = u[3 * o + r];
+    }
+    CUDA_TRY(cudaMemcpy(b->d_u.p, h.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_info(const fe2_batch *b, int32_t *n_rve, int64_t *n_nodes,
+                                     int64_t *n_elems, int32_t *launches) {
+    if (!b) return fail(FE2_EINVAL, "NULL batch");
+    if (n_rve) *n_rve = b->n_rve;
+    if (n_nodes) *n_nodes = b->n_nodes;
+    if (n_elems) *n_elems = b->n_elems;
+    if (launches) *launches = b->last_launches;
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_destroy(fe2_batch *b) {
+    if (!b) return FE2_OK;
+    if (b->solved && b->last_stream) cudaStreamSynchronize(b->last_stream);
+    cudaDeviceSynchronize();
+    b->release();
+    delete b;
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_solve_naive(fe2_batch *b, const double *F, const fe2_opts *opts,
+                                            void *stream) {
+    if (!b || !F) return fail(FE2_EINVAL, "NULL batch or F");
+    fe2_opts o;
+    if (opts) o = *opts; else fe2_opts_default(&o);
+    fe2_status s = check_opts(o);
+    if (s != FE2_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t nmax = 0;
+    for (auto &R : b->rve) nmax = std::max<int64_t>(nmax, R.n_nodes);
+    if (!b->d_naive.p) CUDA_TRY(b->d_naive.alloc(6 * nmax + 16));
+    CUDA_TRY(cudaMemcpyAsync(b->d_F.p, F, sizeof(double) * 9 * b->n_rve, cudaMemcpyHostToDevice, st));
+    NaiveScratch W;
+    W.x = b->d_naive.p;
+    W.g = b->d_naive.p + 3 * nmax;
+    W.acc = b->d_naive.p + 6 * nmax;
+    const DevMesh M = b->mesh();
+    const DevState S = b->state();
+    const DevResults R = b->results();
+    std::vector<int64_t> iters(b->n_rve);
+    std::vector<double> rel(b->n_rve);
+    std::vector<int32_t> stat(b->n_rve);
+    int launches = 0;
+    for (int32_t p = 0; p < b->n_rve; ++p) {
+        int stt = 0;
+        const int e = naive_solve_rve(b->rve[p], M, S, R, b->d_F.p, W, o.tol, o.max_iter,
+                                      o.dt_safety, o.init, p, st, &iters[p], &rel[p], &stt);
+        if (e != 0) return fail(FE2_ECUDA, std::string("naive: ") + cudaGetErrorString((cudaError_t)e));
+        stat[p] = stt;
+        launches += 10 + 4 * (int)iters[p];
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->d_iters.p, iters.data(), sizeof(int64_t) * b->n_rve, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_rel.p, rel.data(), sizeof(double) * b->n_rve, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b->d_status.p, stat.data(), sizeof(int32_t) * b->n_rve, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    b->last_launches = launches;
+    b->last_stream = st;
+    b->solved = true;
+    return FE2_OK;
+}

@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 mode follows the oracle's operations in the oracle's order, so the
+trajectory must be bit-identical: equal iteration counts and equal
+displacements; only the stress sum is reassociated (1e-12 relative).
+Mixed mode must stay within 1e-5 relative stress error (Frobenius norm).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import rve_inputs as ri
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2305_07030_gb300 import Batch  # noqa: E402
+
+
+def rel_err(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a - b)
+
+
+def _workload(sizes, seed, ea="lognormal", Fscale=0.02):
+    rng = np.random.default_rng(seed)
+    nets = [ri.random_network(int(n), rng, ea=ea) for n in sizes]
+    F = np.array([ri.symmetric_perturbation(rng, Fscale) for _ in nets])
+    c = np.array([ri.default_damping(n.n_nodes) for n in nets])
+    return ri.Workload("t", nets, F, c)
+
+
+def _solve(w, **opts):
+    with Batch(w.nets, damping=w.damping) as b:
+        b.solve(w.F, **opts)
+        out = b.stress()
+        out["u"] = b.displacement()
+        out["node_off"] = b.node_off
+    return out
+
+
+@pytest.mark.parametrize("init", ["affine", "reference"])
+def test_fp64_bitwise_trajectory(init):
+    """Several RVEs (many nodes per thread, ragged tails, uneven sizes)."""
+    w = _workload([37, 300, 777, 1500], seed=11)
+    iv = {"affine": 1, "reference": 0}[init]
+    ref = oracle.solve_batch(w, init=iv, tol=1e-8, max_iter=300000)
+    out = _solve(w, precision="fp64", init=init, tol=1e-8, max_iter=300000)
+    for p, r in enumerate(ref):
+        a, b = out["node_off"][p], out["node_off"][p + 1]
+        assert out["status"][p] == r["status"]
+        assert out["iters"][p] == r["iters"], (p, out["iters"][p], r["iters"])
+        assert np.array_equal(out["u"][a:b], r["u"]), np.abs(out["u"][a:b] - r["u"]).max()
+        assert rel_err(out["sigma"][p], r["sigma"]) <= 1e-12
+        assert abs(out["rel_res"][p] - r["rel_res"]) <= 1e-12 * max(r["rel_res"], 1e-300) + 1e-300
+
+
+def test_fp64_global_scratch_class_and_maxiter():
+    """An RVE too big to stage in shared memory runs from L2 scratch; the
+    trajectory is still the oracle's (checked after a fixed iteration cap)."""
+    w = _workload([10500], seed=12)
+    ref = oracle.solve_batch(w, init=1, max_iter=400)
+    out = _solve(w, precision="fp64", max_iter=400)
+    assert out["status"][0] == "MAXITER" and ref[0]["status"] == "MAXITER"
+    assert out["iters"][0] == 400
+    assert np.array_equal(out["u"], ref[0]["u"])
+    assert rel_err(out["sigma"][0], ref[0]["sigma"]) <= 1e-12
+
+
+def test_mixed_within_tolerance():
+    w = _workload([200, 512, 1200, 3000], seed=13)
+    ref = oracle.solve_batch(w, init=1, tol=1e-8)
+    out = _solve(w, precision="mixed", tol=1e-8)
+    errs = [rel_err(out["sigma"][p], r["sigma"]) for p, r in enumerate(ref)]
+    print("mixed stress errors", errs, "iters", list(out["iters"]), [r["iters"] for r in ref])
+    for p in range(w.n_rve):
+        assert out["status"][p] == "OK"
+        assert errs[p] <= 1e-5, errs
+
+
+def test_single_512_node_rve_both_modes():
+    """The 512-node RVE with EA = 1 and F = diag(1.05, 1, 1)."""
+    w = ri.single_rve_512()
+    ref = oracle.solve_batch(w, init=1)[0]
+    out = _solve(w, precision="fp64")
+    assert out["iters"][0] == ref["iters"]
+    assert np.array_equal(out["u"], ref["u"])
+    assert rel_err(out["sigma"][0], ref["sigma"]) <= 1e-12
+    out = _solve(w, precision="mixed")
+    e = rel_err(out["sigma"][0], ref["sigma"])
+    print("512-node mixed error", e, out["iters"][0], ref["iters"])
+    assert out["status"][0] == "OK" and e <= 1e-5
+
+
+def test_edge_cases():
+    rng = np.random.default_rng(14)
+    base = ri.random_network(80, rng)
+    # isolated free node (treated as fixed) and an RVE without elements
+    X = np.vstack([base.X, [[0.5, 0.5, 0.5]]])
+    iso = ri.Network(X=X, elems=base.elems, EA=base.EA,
+                     fixed=np.append(base.fixed, 0).astype(np.uint8))
+    empty = ri.Network(X=rng.random((5, 3)), elems=np.zeros((0, 2), np.int32),
+                       EA=np.zeros(0), fixed=np.zeros(5, np.uint8))
+    chain = ri.Network(X=np.array([[0, 0, 0], [0.5, 0, 0], [1.0, 0, 0]]),
+                       elems=np.array([[0, 1], [1, 2]], np.int32), EA=np.array([1.0, 2.0]),
+                       fixed=np.array([1, 0, 1], np.uint8))
+    nets = [iso, empty, chain, base]
+    F = np.array([ri.symmetric_perturbation(rng), np.eye(3), np.diag([1.1, 1, 1]), np.eye(3)])
+    c = np.array([0.01, 0.01, 0.125, 0.01])
+    w = ri.Workload("edge", nets, F, c)
+    ref = oracle.solve_batch(w, init=1)
+    out = _solve(w, precision="fp64")
+    for p, r in enumerate(ref):
+        a, b = out["node_off"][p], out["node_off"][p + 1]
+        assert out["status"][p] == r["status"] == "OK"
+        assert out["iters"][p] == r["iters"]
+        assert np.array_equal(out["u"][a:b], r["u"])
+    assert out["iters"][1] == 1 and np.all(out["sigma"][1] == 0)
+    assert out["iters"][3] == 1 and np.all(out["sigma"][3] == 0)  # F = I
+    # non-finite F is reported per RVE, not as a call failure
+    F2 = F.copy()
+    F2[2, 0, 0] = np.nan
+    out = _solve(ri.Workload("nan", nets, F2, c), precision="mixed", max_iter=50)
+    assert out["status"][2] == "NAN"
+    assert out["status"][0] == "OK"
+
+
+def test_alone_equals_in_the_mix():
+    """Batching does not change any RVE's result (FP64: bitwise)."""
+    w = _workload([60, 900, 150, 2600, 400, 75], seed=15)
+    mix = _solve(w, precision="fp64")
+    for p in (1, 4):
+        alone = _solve(w.subset([p]), precision="fp64")
+        assert alone["iters"][0] == mix["iters"][p]
+        assert np.array_equal(alone["sigma"][0], mix["sigma"][p])
+    mixm = _solve(w, precision="mixed")
+    alone = _solve(w.subset([3]), precision="mixed")
+    assert alone["iters"][0] == mixm["iters"][3]
+    assert np.array_equal(alone["sigma"][0], mixm["sigma"][3])
+
+
+def test_warm_start_matches_oracle():
+    w = _workload([400, 900], seed=16)
+    with Batch(w.nets, damping=w.damping) as b:
+        b.solve(w.F, precision="fp64")
+        first = b.stress()
+        u1 = b.displacement()
+        F2 = np.array([np.diag([1.005, 1, 1]) @ f for f in w.F])
+        b.solve(F2, precision="fp64", init="warm")
+        second = b.stress()
+        u2 = b.displacement()
+    off = np.concatenate([[0], np.cumsum([n.n_nodes for n in w.nets])])
+    for p, net in enumerate(w.nets):
+        r = oracle.solve(net, F2[p], w.damping[p], init=2, u_warm=u1[off[p]:off[p + 1]])
+        assert second["iters"][p] == r["iters"]
+        assert np.array_equal(u2[off[p]:off[p + 1]], r["u"])
+        assert second["iters"][p] < first["iters"][p]
+
+
+def test_device_entry_points():
+    w = _workload([300, 500], seed=17)
+    with Batch(w.nets, damping=w.damping) as b:
+        F_dev = torch.tensor(w.F.reshape(-1), dtype=torch.float64, device="cuda")
+        s = torch.cuda.Stream()
+        b.solve_dev(F_dev, stream=s, precision="fp64")
+        sig = torch.zeros(9 * w.n_rve, dtype=torch.float64, device="cuda")
+        it = torch.zeros(w.n_rve, dtype=torch.int64, device="cuda")
+        b.results_dev(sigma_dev=sig, iters_dev=it, stream=s)
+        s.synchronize()
+        host = b.stress()
+        assert np.array_equal(sig.cpu().numpy().reshape(-1, 3, 3), host["sigma"])
+        assert np.array_equal(it.cpu().numpy(), host["iters"])
+        assert b.info()["launches"] >= 1
+
+
+def test_naive_path_matches_oracle():
+    """The paper's naive launch loop (atomic scatter: rounding order differs)."""
+    w = _workload([150, 260], seed=18)
+    ref = oracle.solve_batch(w, init=1)
+    with Batch(w.nets, damping=w.damping) as b:
+        b.solve_naive(w.F, init="affine")
+        out = b.stress()
+    for p, r in enumerate(ref):
+        assert out["status"][p] == "OK"
+        assert abs(out["iters"][p] - r["iters"]) <= 0.05 * r["iters"] + 2
+        assert rel_err(out["sigma"][p], r["sigma"]) <= 1e-6
+
+
+def test_invalid_inputs_rejected():
+    from paper_2305_07030_gb300 import FE2Error
+    rng = np.random.default_rng(19)
+    net = ri.random_network(30, rng)
+    bad = ri.Network(X=net.X, elems=np.vstack([net.elems, net.elems[:1]]),
+                     EA=np.append(net.EA, 1.0), fixed=net.fixed)
+    with pytest.raises(FE2Error, match="repeats"):
+        Batch([bad])
+    bad = ri.Network(X=net.X, elems=np.array([[0, 0]], np.int32), EA=np.ones(1), fixed=net.fixed)
+    with pytest.raises(FE2Error, match="itself"):
+        Batch([bad])
+    bad = ri.Network(X=net.X, elems=net.elems, EA=-net.EA, fixed=net.fixed)
+    with pytest.raises(FE2Error, match="EA"):
+        Batch([bad])
+    bad = ri.Network(X=net.X, elems=np.array([[0, 99]], np.int32), EA=np.ones(1), fixed=net.fixed)
+    with pytest.raises(FE2Error, match="range"):
+        Batch([bad])
+    with Batch([net]) as b:
+        with pytest.raises(FE2Error):
+            b.solve(np.eye(3)[None], max_iter=0)
