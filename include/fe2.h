@@ -176,6 +176,14 @@ fe2_status fe2_batch_destroy(fe2_batch *b);
 fe2_status fe2_batch_info(const fe2_batch *b, int32_t *n_rve, int64_t *n_nodes,
                           int64_t *n_elems, int32_t *launches);
 
+/* Device time of each persistent launch of the last batched solve, measured
+ * with CUDA events recorded on the stream that launched it (one entry per
+ * size class; classes run concurrently). Waits for those launches.
+ *   ms   out: up to `cap` durations in milliseconds
+ *   n    out: number of timed launches (may exceed cap)
+ * FE2_ESTATE before the first solve; after a naive solve *n = 0. */
+fe2_status fe2_batch_kernel_times(fe2_batch *b, float *ms, int32_t cap, int32_t *n);
+
 /*
  * The paper's naive path (Section III): the same FP64 algorithm solved one RVE
  * after another, each iteration as a short sequence of kernel launches

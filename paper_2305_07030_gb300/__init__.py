@@ -53,17 +53,29 @@ def _load():
     lib.fe2_batch_set_displacement.argtypes = [P, P]
     lib.fe2_batch_destroy.argtypes = [P]
     lib.fe2_batch_info.argtypes = [P, P, P, P, P]
+    lib.fe2_batch_kernel_times.argtypes = [P, P, I32, P]
+    lib.fe2_probe_smem_bandwidth.argtypes = [P, P]
+    lib.fe2_probe_smem_bandwidth.restype = C.c_int
     lib.fe2_last_error.argtypes = []
     lib.fe2_last_error.restype = C.c_char_p
     for name in ("fe2_batch_create", "fe2_batch_solve", "fe2_batch_solve_dev",
                  "fe2_batch_solve_naive", "fe2_batch_stress", "fe2_batch_results_dev",
                  "fe2_batch_get_displacement", "fe2_batch_set_displacement",
-                 "fe2_batch_destroy", "fe2_batch_info"):
+                 "fe2_batch_destroy", "fe2_batch_info", "fe2_batch_kernel_times"):
         getattr(lib, name).restype = C.c_int
     return lib
 
 
 _lib = _load()
+
+
+def probe_smem_bandwidth():
+    """Measured aggregate shared-memory read bandwidth (GB/s) and max SM clock (MHz)."""
+    g, c = C.c_double(), C.c_double()
+    rc = _lib.fe2_probe_smem_bandwidth(C.byref(g), C.byref(c))
+    if rc != 0:
+        raise FE2Error(3, f"smem probe failed ({rc})")
+    return g.value, c.value
 
 
 def last_error() -> str:
@@ -186,6 +198,13 @@ class Batch:
         a, b, c, d = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
         _check(_lib.fe2_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
         return {"n_rve": a.value, "n_nodes": b.value, "n_elems": c.value, "launches": d.value}
+
+    def kernel_times_ms(self):
+        """Event-timed duration of each persistent launch of the last solve."""
+        buf = np.zeros(16, np.float32)
+        n = C.c_int32()
+        _check(_lib.fe2_batch_kernel_times(self._h, _ptr(buf), 16, C.byref(n)))
+        return [float(x) for x in buf[:min(n.value, 16)]]
 
     def close(self):
         if getattr(self, "_h", None):

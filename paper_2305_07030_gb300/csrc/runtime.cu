@@ -89,9 +89,11 @@ struct fe2_batch {
     std::vector<SizeClass> classes_fp64, classes_mixed;
     bool solved = false;
     int32_t last_launches = 0;
+    int32_t last_timed = 0;            // persistent launches bracketed by tev
     cudaStream_t last_stream = nullptr;
     std::vector<cudaStream_t> side;  // forked streams for concurrent classes
     std::vector<cudaEvent_t> ev;
+    std::vector<cudaEvent_t> tev;      // timing events around each class launch
     DevBuf<double> d_naive;           // naive comparator scratch (allocated on first use)
     double *h_F = nullptr;             // pinned staging for F
     cudaEvent_t ev_F = nullptr;        // completion of the last F upload
@@ -145,8 +147,10 @@ struct fe2_batch {
         ev_F = nullptr;
         for (auto s : side) cudaStreamDestroy(s);
         for (auto e : ev) cudaEventDestroy(e);
+        for (auto e : tev) cudaEventDestroy(e);
         side.clear();
         ev.clear();
+        tev.clear();
     }
 };
 
@@ -467,6 +471,11 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         A(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         if (rc == FE2_OK) b->ev.push_back(e);
     }
+    for (int k = 0; k < 12 && rc == FE2_OK; ++k) {
+        cudaEvent_t e;
+        A(cudaEventCreate(&e), "timing event");
+        if (rc == FE2_OK) b->tev.push_back(e);
+    }
     if (rc != FE2_OK) {
         b->release();
         delete b;
@@ -523,14 +532,17 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
                           : occupancy_dr_mixed(c.smem_positions, block, smem);
         per_sm = std::max(1, per_sm);
         const int grid = std::max(1, std::min<int>((int)c.rves.size(), per_sm * b->sm_count));
+        CUDA_TRY(cudaEventRecord(b->tev[2 * k], s));
         const int e = fp64 ? launch_dr_fp64(M, S, R, P, grid, block, smem, s)
                            : launch_dr_mixed(M, S, R, P, grid, block, smem, s);
+        CUDA_TRY(cudaEventRecord(b->tev[2 * k + 1], s));
         if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
         ++launches;
         CUDA_TRY(cudaEventRecord(b->ev[1 + k], s));
         CUDA_TRY(cudaStreamWaitEvent(st, b->ev[1 + k], 0));
     }
     b->last_launches = launches;
+    b->last_timed = launches;
     b->last_stream = st;
     b->solved = true;
     return FE2_OK;
@@ -632,6 +644,17 @@ extern "C" fe2_status fe2_batch_info(const fe2_batch *b, int32_t *n_rve, int64_t
     return FE2_OK;
 }
 
+extern "C" fe2_status fe2_batch_kernel_times(fe2_batch *b, float *ms, int32_t cap, int32_t *n) {
+    if (!b || !n) return fail(FE2_EINVAL, "NULL batch or n");
+    if (!b->solved) return fail(FE2_ESTATE, "no solve has been issued");
+    *n = b->last_timed;
+    for (int32_t k = 0; k < b->last_timed && k < cap; ++k) {
+        CUDA_TRY(cudaEventSynchronize(b->tev[2 * k + 1]));
+        CUDA_TRY(cudaEventElapsedTime(ms + k, b->tev[2 * k], b->tev[2 * k + 1]));
+    }
+    return FE2_OK;
+}
+
 extern "C" fe2_status fe2_batch_destroy(fe2_batch *b) {
     if (!b) return FE2_OK;
     if (b->solved && b->last_stream) cudaStreamSynchronize(b->last_stream);
@@ -677,6 +700,7 @@ extern "C" fe2_status fe2_batch_solve_naive(fe2_batch *b, const double *F, const
     CUDA_TRY(cudaMemcpyAsync(b->d_status.p, stat.data(), sizeof(int32_t) * b->n_rve, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     b->last_launches = launches;
+    b->last_timed = 0;
     b->last_stream = st;
     b->solved = true;
     return FE2_OK;
