@@ -60,13 +60,14 @@ typedef enum {
      * in the same order as a serial element-scatter implementation in the
      * caller's node order, no fused multiply-add, correctly rounded sqrt and
      * divide. The trajectory is bit for bit that of such an implementation;
-     * only the residual and stress sums are reassociated. */
+     * only the residual and stress sums are reassociated. One CTA per RVE. */
     FE2_PREC_FP64 = 0,
-    /* FP32 force and update arithmetic on the FP32 pipes: a double-float lead
-     * phase for the first lead_iters iterations (where the network picks its
+    /* All arithmetic on the FP32 pipes, one thread-block cluster per RVE: a
+     * double-float (FP32 pair) lead phase until the relative residual first
+     * drops below lead_tol (the transient in which the network picks its
      * equilibrium), then FP32 increments of the element forces about a
-     * double-float reference state that is refreshed every rebase_every
-     * iterations. Residual test and stress sum are FP64. */
+     * double-float reference state refreshed every rebase_every iterations.
+     * Residual test and stress sum are FP64. */
     FE2_PREC_MIXED = 1
 } fe2_precision;
 
@@ -87,11 +88,14 @@ typedef struct {
     int32_t kinetic_energy; /* 1: also track the kinetic energy 1/2 sum m v^2 */
     int32_t block_threads;  /* threads per CTA: 0 = default (512, the paper's
                                team size), else a multiple of 32 in [64, 512] */
-    int64_t lead_iters;   /* MIXED: double-float iterations before the FP32
-                             phase; < 0 = default 1000 (n/512)^(1/3) */
+    int64_t lead_iters;   /* MIXED: < 0 = lead until the relative residual
+                             <= lead_tol (default); >= 0 = exactly that many
+                             double-float iterations */
     int32_t rebase_every; /* MIXED: FP32 iterations between double-float
                              reference refreshes; <= 0 = default 512 */
     int32_t reserved;
+    double lead_tol;      /* MIXED: relative residual that ends the lead
+                             phase (default 1e-3) */
 } fe2_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -159,6 +163,16 @@ fe2_status fe2_batch_stress(fe2_batch *b, double *sigma, int64_t *iters, double 
  * into DEVICE buffers (any may be NULL). Same layouts as fe2_batch_stress(). */
 fe2_status fe2_batch_results_dev(fe2_batch *b, double *sigma_dev, int64_t *iters_dev,
                                  double *rel_res_dev, int32_t *status_dev, void *stream);
+
+/* Per-RVE diagnostics of the last batched solve (HOST memory, any may be
+ * NULL): the residual scale f_ref = max(||g(F X)||, ||g(x0)||) over all DOFs,
+ * the final kinetic energy (0 unless opts.kinetic_energy), and the number of
+ * double-float lead iterations (MIXED; 0 for FP64). Waits for the solve. */
+fe2_status fe2_batch_diagnostics(fe2_batch *b, double *f_ref, double *kinetic_energy,
+                                 int64_t *lead_iters);
+
+/* Cluster size (CTAs) the MIXED solver uses for each RVE (n_rve entries). */
+fe2_status fe2_batch_parts(const fe2_batch *b, int32_t *parts);
 
 /* Copy the current displacement u = x - X (3*N doubles, caller's node order
  * and numbering) to HOST memory. Waits for the last solve. */

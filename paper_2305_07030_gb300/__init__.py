@@ -32,7 +32,7 @@ class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("dt_safety", C.c_double),
                 ("precision", C.c_int32), ("init", C.c_int32), ("kinetic_energy", C.c_int32),
                 ("block_threads", C.c_int32), ("lead_iters", C.c_int64),
-                ("rebase_every", C.c_int32), ("reserved", C.c_int32)]
+                ("rebase_every", C.c_int32), ("reserved", C.c_int32), ("lead_tol", C.c_double)]
 
 
 def _load():
@@ -54,6 +54,8 @@ def _load():
     lib.fe2_batch_destroy.argtypes = [P]
     lib.fe2_batch_info.argtypes = [P, P, P, P, P]
     lib.fe2_batch_kernel_times.argtypes = [P, P, I32, P]
+    lib.fe2_batch_diagnostics.argtypes = [P, P, P, P]
+    lib.fe2_batch_parts.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.restype = C.c_int
     lib.fe2_last_error.argtypes = []
@@ -61,7 +63,8 @@ def _load():
     for name in ("fe2_batch_create", "fe2_batch_solve", "fe2_batch_solve_dev",
                  "fe2_batch_solve_naive", "fe2_batch_stress", "fe2_batch_results_dev",
                  "fe2_batch_get_displacement", "fe2_batch_set_displacement",
-                 "fe2_batch_destroy", "fe2_batch_info", "fe2_batch_kernel_times"):
+                 "fe2_batch_destroy", "fe2_batch_info", "fe2_batch_kernel_times",
+                 "fe2_batch_diagnostics", "fe2_batch_parts"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -96,7 +99,8 @@ _INIT = {"reference": 0, "affine": 1, "warm": 2}
 
 
 def make_opts(tol=1e-8, max_iter=10_000_000, dt_safety=0.9, precision="mixed", init="affine",
-              kinetic_energy=False, block_threads=0, lead_iters=-1, rebase_every=0) -> Opts:
+              kinetic_energy=False, block_threads=0, lead_iters=-1, rebase_every=0,
+              lead_tol=1e-3) -> Opts:
     o = Opts()
     _lib.fe2_opts_default(C.byref(o))
     o.tol = float(tol)
@@ -108,6 +112,7 @@ def make_opts(tol=1e-8, max_iter=10_000_000, dt_safety=0.9, precision="mixed", i
     o.block_threads = int(block_threads)
     o.lead_iters = int(lead_iters)
     o.rebase_every = int(rebase_every)
+    o.lead_tol = float(lead_tol)
     return o
 
 
@@ -198,6 +203,17 @@ class Batch:
         a, b, c, d = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
         _check(_lib.fe2_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
         return {"n_rve": a.value, "n_nodes": b.value, "n_elems": c.value, "launches": d.value}
+
+    def diagnostics(self):
+        P = self.n_rve
+        fr, ke, ld = np.zeros(P), np.zeros(P), np.zeros(P, np.int64)
+        _check(_lib.fe2_batch_diagnostics(self._h, _ptr(fr), _ptr(ke), _ptr(ld)))
+        return {"f_ref": fr, "kinetic_energy": ke, "lead_iters": ld}
+
+    def parts(self):
+        out = np.zeros(self.n_rve, np.int32)
+        _check(_lib.fe2_batch_parts(self._h, _ptr(out)))
+        return out
 
     def kernel_times_ms(self):
         """Event-timed duration of each persistent launch of the last solve."""

@@ -1,338 +1,562 @@
-// Mixed-precision dynamic relaxation (Algorithm 1) for a batch of RVEs: one CTA
-// per RVE, whole loop in one persistent launch.
+// Mixed-precision dynamic relaxation (Algorithm 1) for a batch of RVEs: one
+// thread-block cluster per RVE, whole loop inside one persistent launch.
 //
-// Phase 1 (lead): the first lead_iters iterations run in FP64 exactly like the
-// FP64 kernel. Random fiber networks are not isostatic and can pass bifurcation
-// points (Section II); which equilibrium the relaxation settles into is decided
-// early in the transient and is sensitive to force errors far below FP32
-// rounding, so the lead keeps that choice the reference one.
+// Layout. The RVE is split spatially into `parts` pieces, one per CTA of the
+// cluster; a CTA stages the current positions of its own nodes in its shared
+// memory and reads neighbours owned by other CTAs through distributed shared
+// memory. The paper used one thread team per sub-problem (Section III); a
+// cluster lets one sub-problem span several SMs when one team is not enough.
 //
-// Phase 2 (FP32 increments): every element force is written as an exact
-// increment about a reference state x_ref,
-//     t(d_ref + dd) = t(d_ref) + q_ref dd + dq (d_ref + dd),
-//     q = N/l = EA (1/L - 1/l),  dq = EA h / (l l_ref (l + l_ref)),
-//     h = l^2 - l_ref^2 = 2 d_ref.dd + dd.dd,
-// in which every FP32 operation acts on small quantities. The nodal sum of
-// t(d_ref) (g_ref) is evaluated in FP64 and refreshed every rebase_every
-// iterations, when the FP32 displacement increment du is folded into the FP64
-// displacement. Updates (velocity, displacement increment, damping,
-// acceleration) are FP32; the residual norm is accumulated per warp in FP32
-// (a sum of squares, no cancellation) and across warps in FP64; the
-// convergence test and the stress sum are FP64.
+// Precision. All arithmetic runs on the FP32 pipes (GB300's FP64 rate is a
+// small fraction of FP32):
+//  * lead phase: double-float (hi + lo FP32 pairs, ~48 bits) positions,
+//    velocities, accelerations and element forces until the relative residual
+//    first drops below lead_tol. Random fiber networks are not isostatic and
+//    can pass bifurcation points (Section II); which equilibrium the
+//    relaxation settles into is decided in this transient and is sensitive to
+//    force errors far below FP32 rounding;
+//  * FP32 phase: each element force is an exact increment about a reference
+//    state x_ref,
+//        t(d_ref + dd) = t(d_ref) + q_ref dd + dq (d_ref + dd),
+//        q = N/l = EA (1/L - 1/l),  dq = EA h / (l l_ref (l + l_ref)),
+//        h = l^2 - l_ref^2 = 2 d_ref.dd + dd.dd,
+//    so every FP32 operation acts on small quantities; the nodal sums of
+//    t(d_ref) (g_ref) are evaluated in double-float every rebase_every
+//    iterations, when the FP32 increment du is folded into the double-float
+//    displacement. Velocity and increment updates are FP32;
+//  * the residual norm is summed per warp in FP32 (squares, no cancellation)
+//    and across warps and CTAs in FP64; the convergence test and the stress
+//    sum are FP64.
+//
+// Synchronisation. The FP32 phase keeps two increment buffers (ping-pong), so
+// one cluster barrier per iteration suffices: iteration n writes buffer n&1,
+// the barrier publishes it, and the residual of iteration n-1 is tested right
+// after that barrier (its state, buffer (n-1)&1, is still intact).
+#include <cooperative_groups.h>
+
+#include "df64.cuh"
 #include "dr_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fe2 {
 
-__device__ __forceinline__ double block_sum_f(float v, double *red) {
+namespace {
+
+constexpr int kMaxWarps = 16;  // blocks of at most 512 threads
+
+struct MixedShared {
+    double red[2][kMaxParts][kMaxWarps];  // per-warp residual partials of every CTA
+    double kred[2][kMaxParts][kMaxWarps]; // kinetic-energy partials
+    double sig[kMaxParts][9];             // stress partials, read by rank 0
+    double wsum[kMaxWarps][9];            // per-warp stress partials
+    float4 *P[kMaxParts];                 // every CTA's x_ref / position-hi array
+    float4 *Q[2][kMaxParts];              // every CTA's increment / position-lo arrays
+    double *redp[kMaxParts];              // every CTA's red
+    double *kredp[kMaxParts];             // every CTA's kred
+    double *sigp;                         // rank 0's sig
+    int item;
+};
+
+struct Part {
+    int me, C;
+    int f0, nfr;   // own free nodes: RVE-local [f0, f0 + nfr)
+    int g0, nfx;   // own fixed nodes: RVE-local n_free + [g0, g0 + nfx)
+    int nf;        // RVE free count
+    __device__ int gidx(int k) const { return k < nfr ? f0 + k : nf + g0 + (k - nfr); }
+    __device__ int m() const { return nfr + nfx; }
+};
+
+// Sum of one FP32 value per thread over the whole cluster; every thread gets
+// the FP64 total. Includes one cluster barrier. Alternate `buf` between calls.
+__device__ __forceinline__ double cluster_sum(cg::cluster_group &cl, MixedShared &sh, const Part &pt,
+                                              float v, int buf, bool want_k, float kv, double *kout) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (want_k)
+        for (int o = 16; o > 0; o >>= 1) kv += __shfl_xor_sync(0xffffffffu, kv, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < pt.C) {
+        sh.redp[lane][(buf * kMaxParts + pt.me) * kMaxWarps + warp] = (double)v;
+        if (want_k) sh.kredp[lane][(buf * kMaxParts + pt.me) * kMaxWarps + warp] = (double)kv;
+    }
+    cl.sync();
     const int nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) red[warp] = (double)v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += red[w];
-    __syncthreads();
+    double t = 0.0, tk = 0.0;
+    for (int r = 0; r < pt.C; ++r)
+        for (int w = 0; w < nw; ++w) {
+            t += sh.red[buf][r][w];
+            if (want_k) tk += sh.kred[buf][r][w];
+        }
+    if (want_k) *kout = tk;
     return t;
 }
 
-__device__ __forceinline__ int64_t default_lead(int n) {
-    return (int64_t)(1000.0 * cbrt((double)n / 512.0));
+// Double-float internal force on own node k (Algorithm 1, getInternalForces),
+// gathered over its CSR row: g = sum_j EA (1/L - 1/l) (x_j - x_i).
+__device__ __forceinline__ void gather_df(const DevMesh &M, const RveDesc &R, const int32_t *rowptr,
+                                          const MixedShared &sh, const Part &pt, int k,
+                                          const float4 *Pl, const float4 *Ql, int qbuf, df &g0,
+                                          df &g1, df &g2) {
+    const int gi = pt.gidx(k);
+    const float4 pi = Pl[k], qi = Ql[k];
+    const df xi0 = {pi.x, qi.x}, xi1 = {pi.y, qi.y}, xi2 = {pi.z, qi.z};
+    g0 = df_from(0.f); g1 = df_from(0.f); g2 = df_from(0.f);
+    const int beg = rowptr[gi], end = rowptr[gi + 1];
+    for (int e = beg; e < end; ++e) {
+        const int64_t kk = R.csr0 + e;
+        const int cp = M.col_part[kk];
+        const int r = cp >> 16, loc = cp & 0xffff;
+        const float4 pj = r == pt.me ? Pl[loc] : sh.P[r][loc];
+        const float4 qj = r == pt.me ? Ql[loc] : sh.Q[qbuf][r][loc];
+        const df d0 = df_sub({pj.x, qj.x}, xi0);
+        const df d1 = df_sub({pj.y, qj.y}, xi1);
+        const df d2 = df_sub({pj.z, qj.z}, xi2);
+        const df l2 = df_add(df_add(df_sqr(d0), df_sqr(d1)), df_sqr(d2));
+        const df rl = df_rsqrt(l2);
+        const float2 eh = M.eaf[kk], el = M.eaf_lo[kk];
+        const df q = df_mul({eh.x, el.x}, df_sub({eh.y, el.y}, rl));
+        g0 = df_add(g0, df_mul(q, d0));
+        g1 = df_add(g1, df_mul(q, d1));
+        g2 = df_add(g2, df_mul(q, d2));
+    }
 }
 
-template <bool SM>
-__device__ void solve_rve_mixed(const DevMesh &M, const DevState &S, const DevResults &O,
-                                const SolveParams &P, int p, unsigned char *smem, double *red) {
+__device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M,
+                                const DevState &S, const DevResults &O, const SolveParams &P,
+                                int p, float4 *Pl, float4 *Q0, float4 *Q1, int &rb) {
     const RveDesc R = M.rve[p];
     const int n = R.n_nodes, nf = R.n_free;
-    const int64_t n0 = R.node0;
+    const int64_t n0 = R.node0, b3 = 3 * n0;
     const int32_t *rowptr = M.rowptr + R.rp0;
-    unsigned char *base = SM ? smem : reinterpret_cast<unsigned char *>(S.pg + 2 * n0);
-    // FP64 view (24 B/node) and FP32 view (2 float4 = 32 B/node) of one buffer.
-    double *x0 = reinterpret_cast<double *>(base), *x1 = x0 + n, *x2 = x1 + n;
-    float4 *Pq = reinterpret_cast<float4 *>(base);  // x_ref (FP32)
-    float4 *Qq = Pq + n;                            // du (FP32)
+    const int32_t *po = M.part_off + (int64_t)p * 2 * (kMaxParts + 1);
+    Part pt;
+    pt.me = (int)cl.block_rank();
+    pt.C = (int)cl.num_blocks();
+    pt.nf = nf;
+    pt.f0 = po[pt.me];
+    pt.nfr = po[pt.me + 1] - pt.f0;
+    pt.g0 = po[kMaxParts + 1 + pt.me];
+    pt.nfx = po[kMaxParts + 1 + pt.me + 1] - pt.g0;
+    const int m = pt.m();
     double F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = P.F[9 * (int64_t)p + k];
-    const double *X0 = M.X0 + n0, *X1 = M.X1 + n0, *X2 = M.X2 + n0;
-    double *u0 = S.u0 + n0, *u1 = S.u1 + n0, *u2 = S.u2 + n0;
-    double *v0 = S.v0 + n0, *v1 = S.v1 + n0, *v2 = S.v2 + n0;
-    double *a0 = S.a0 + n0, *a1 = S.a1 + n0, *a2 = S.a2 + n0;
-    const double *mass = M.mass + n0;
-    const float *inv_m = M.inv_mass_f + n0;
-    float *fv = S.fv + 3 * n0, *fa = S.fa + 3 * n0, *fg = S.fg + 3 * n0;  // [3][n] per RVE
+    // per-RVE [3][n] blocks
+    const float *Xh = M.Xh + b3, *Xl = M.Xl + b3;
+    float *uh = S.uh + b3, *ul = S.ul + b3, *vh = S.vh + b3, *vl = S.vl + b3;
+    float *ah = S.ah + b3, *al = S.al + b3, *fg = S.fg + b3;
+    const float *imh = M.imh + n0, *iml = M.iml + n0;
+    double *xg = S.xg + b3;
+    const bool want_k = P.want_ke != 0;
+    float4 *Qb[2] = {Q0, Q1};
 
-    // ---- setup, identical to the FP64 kernel ----
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double X[3] = {X0[i], X1[i], X2[i]};
-        x0[i] = dadd(dadd(dmul(F[0], X[0]), dmul(F[1], X[1])), dmul(F[2], X[2]));
-        x1[i] = dadd(dadd(dmul(F[3], X[0]), dmul(F[4], X[1])), dmul(F[5], X[2]));
-        x2[i] = dadd(dadd(dmul(F[6], X[0]), dmul(F[7], X[1])), dmul(F[8], X[2]));
-    }
-    __syncthreads();
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double g0, g1, g2;
-        gather_force_fp64(M, rowptr, R.csr0, i, x0, x1, x2, g0, g1, g2);
-        acc += dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
-    }
-    const double f_aff = dsqrt(block_sum(acc, red));
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const bool fixed = i >= nf;
-        const double X[3] = {X0[i], X1[i], X2[i]};
-        double u[3];
+    // ---- setup: affine positions, f_ref, initial state (Algorithm 1) ----
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int i = pt.gidx(k);
+        const double X[3] = {M.X0[n0 + i], M.X1[n0 + i], M.X2[n0 + i]};
+        double xa[3];
+        for (int r = 0; r < 3; ++r)
+            xa[r] = dadd(dadd(dmul(F[3 * r], X[0]), dmul(F[3 * r + 1], X[1])), dmul(F[3 * r + 2], X[2]));
+        const df a0 = df_from_double(xa[0]), a1 = df_from_double(xa[1]), a2 = df_from_double(xa[2]);
+        Pl[k] = make_float4(a0.hi, a1.hi, a2.hi, 0.f);
+        Q0[k] = make_float4(a0.lo, a1.lo, a2.lo, 0.f);
+        const bool fixed = k >= pt.nfr;
+        const double *uw[3] = {S.u0 + n0, S.u1 + n0, S.u2 + n0};
         for (int r = 0; r < 3; ++r) {
-            const double xa = r == 0 ? x0[i] : (r == 1 ? x1[i] : x2[i]);
-            const double uaff = dsub(xa, X[r]);
-            if (fixed || P.init == 1) u[r] = uaff;
-            else if (P.init == 2) u[r] = (r == 0 ? u0[i] : (r == 1 ? u1[i] : u2[i]));
-            else u[r] = 0.0;
-        }
-        u0[i] = u[0]; u1[i] = u[1]; u2[i] = u[2];
-        if (!fixed) { v0[i] = 0.0; v1[i] = 0.0; v2[i] = 0.0; }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        x0[i] = dadd(X0[i], u0[i]);
-        x1[i] = dadd(X1[i], u1[i]);
-        x2[i] = dadd(X2[i], u2[i]);
-    }
-    __syncthreads();
-    acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double g0, g1, g2;
-        gather_force_fp64(M, rowptr, R.csr0, i, x0, x1, x2, g0, g1, g2);
-        acc += dadd(dadd(dmul(g0, g0), dmul(g1, g1)), dmul(g2, g2));
-        if (i < nf) {
-            const double m = mass[i];
-            a0[i] = ddiv(g0, m); a1[i] = ddiv(g1, m); a2[i] = ddiv(g2, m);
+            const double uaff = dsub(xa[r], X[r]);
+            double u;
+            if (fixed || P.init == 1) u = uaff;
+            else if (P.init == 2) u = uw[r][i];
+            else u = 0.0;
+            const df ud = df_from_double(u);
+            uh[r * n + i] = ud.hi;
+            ul[r * n + i] = ud.lo;
         }
     }
-    const double f0 = dsqrt(block_sum(acc, red));
+    cl.sync();
+    float acc = 0.f;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        df g0, g1, g2;
+        gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g0, g1, g2);
+        acc += g0.hi * g0.hi + g1.hi * g1.hi + g2.hi * g2.hi;
+    }
+    double dummy;
+    const double f_aff = sqrt(cluster_sum(cl, sh, pt, acc, rb, false, 0.f, &dummy));
+    rb ^= 1;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int i = pt.gidx(k);
+        df x[3];
+        for (int r = 0; r < 3; ++r)
+            x[r] = df_add({Xh[r * n + i], Xl[r * n + i]}, {uh[r * n + i], ul[r * n + i]});
+        Pl[k] = make_float4(x[0].hi, x[1].hi, x[2].hi, 0.f);
+        Q0[k] = make_float4(x[0].lo, x[1].lo, x[2].lo, 0.f);
+    }
+    cl.sync();
+    acc = 0.f;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        df g[3];
+        gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g[0], g[1], g[2]);
+        acc += g[0].hi * g[0].hi + g[1].hi * g[1].hi + g[2].hi * g[2].hi;
+        if (k < pt.nfr) {
+            const int i = pt.gidx(k);
+            const df im = {imh[i], iml[i]};
+            for (int r = 0; r < 3; ++r) {
+                const df a = df_mul(g[r], im);
+                ah[r * n + i] = a.hi; al[r * n + i] = a.lo;
+                vh[r * n + i] = 0.f; vl[r * n + i] = 0.f;
+                fg[r * n + i] = g[r].hi;
+            }
+        }
+    }
+    const double f0 = sqrt(cluster_sum(cl, sh, pt, acc, rb, false, 0.f, &dummy));
+    rb ^= 1;
     const double f_ref = f_aff > f0 ? f_aff : f0;
     const double thresh = P.tol * f_ref;
-    const double dt = dmul(P.alpha, R.dtc);
-    const double hdt = dmul(0.5, dt);
-    const double mc = -R.c;
-    const int64_t lead = P.lead_iters >= 0 ? P.lead_iters : default_lead(n);
+    const double lead_thresh = P.lead_tol * f_ref;
+
+    const double dt64 = dmul(P.alpha, R.dtc);
+    const df dt = df_from_double(dt64), hdt = df_from_double(dmul(0.5, dt64));
+    const df cdf = df_from_double(R.c);
+    const float dtf = dt.hi, hdtf = hdt.hi, cf = cdf.hi;
     const int K = P.rebase_every > 0 ? P.rebase_every : 512;
 
-    int64_t it = 0;
+    int64_t it = 0, lead = 0;
     int status = RVE_MAXITER;
     double r = 0.0, ke = 0.0;
     bool done = false;
+    int fin = -1;  // increment buffer holding the final state (FP32 phase), -1: none
 
-    // ---- phase 1: FP64 lead ----
-    while (it < lead) {
-        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            double vv0 = dadd(v0[i], dmul(hdt, a0[i]));
-            double vv1 = dadd(v1[i], dmul(hdt, a1[i]));
-            double vv2 = dadd(v2[i], dmul(hdt, a2[i]));
-            double uu0 = dadd(u0[i], dmul(dt, vv0));
-            double uu1 = dadd(u1[i], dmul(dt, vv1));
-            double uu2 = dadd(u2[i], dmul(dt, vv2));
-            v0[i] = vv0; v1[i] = vv1; v2[i] = vv2;
-            u0[i] = uu0; u1[i] = uu1; u2[i] = uu2;
-            x0[i] = dadd(X0[i], uu0);
-            x1[i] = dadd(X1[i], uu1);
-            x2[i] = dadd(X2[i], uu2);
+    // ---- lead phase: double-float ----
+    for (;;) {
+        for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+            const int i = pt.f0 + k;
+            df x[3];
+            for (int c = 0; c < 3; ++c) {
+                df v = {vh[c * n + i], vl[c * n + i]};
+                const df a = {ah[c * n + i], al[c * n + i]};
+                v = df_add(v, df_mul(hdt, a));
+                df u = {uh[c * n + i], ul[c * n + i]};
+                u = df_add(u, df_mul(dt, v));
+                vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
+                uh[c * n + i] = u.hi; ul[c * n + i] = u.lo;
+                x[c] = df_add({Xh[c * n + i], Xl[c * n + i]}, u);
+            }
+            Pl[k] = make_float4(x[0].hi, x[1].hi, x[2].hi, 0.f);
+            Q0[k] = make_float4(x[0].lo, x[1].lo, x[2].lo, 0.f);
         }
-        __syncthreads();
-        double rs = 0.0, kes = 0.0;
-        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            double g0, g1, g2;
-            gather_force_fp64(M, rowptr, R.csr0, i, x0, x1, x2, g0, g1, g2);
-            const double m = mass[i];
-            const double cm = dmul(mc, m);
-            double vv0 = v0[i], vv1 = v1[i], vv2 = v2[i];
-            rs = dadd(rs, dmul(g0, g0));
-            rs = dadd(rs, dmul(g1, g1));
-            rs = dadd(rs, dmul(g2, g2));
-            const double aa0 = ddiv(dadd(g0, dmul(cm, vv0)), m);
-            const double aa1 = ddiv(dadd(g1, dmul(cm, vv1)), m);
-            const double aa2 = ddiv(dadd(g2, dmul(cm, vv2)), m);
-            vv0 = dadd(vv0, dmul(hdt, aa0));
-            vv1 = dadd(vv1, dmul(hdt, aa1));
-            vv2 = dadd(vv2, dmul(hdt, aa2));
-            a0[i] = aa0; a1[i] = aa1; a2[i] = aa2;
-            v0[i] = vv0; v1[i] = vv1; v2[i] = vv2;
-            if (P.want_ke) kes += 0.5 * m * (vv0 * vv0 + vv1 * vv1 + vv2 * vv2);
+        cl.sync();
+        float rs = 0.f, kes = 0.f;
+        for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+            const int i = pt.f0 + k;
+            df g[3];
+            gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g[0], g[1], g[2]);
+            const df im = {imh[i], iml[i]};
+            float vv = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                df v = {vh[c * n + i], vl[c * n + i]};
+                const df a = df_sub(df_mul(g[c], im), df_mul(cdf, v));
+                v = df_add(v, df_mul(hdt, a));
+                ah[c * n + i] = a.hi; al[c * n + i] = a.lo;
+                vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
+                fg[c * n + i] = g[c].hi;
+                rs += g[c].hi * g[c].hi;
+                vv += v.hi * v.hi;
+            }
+            if (want_k) kes += 0.5f * vv / imh[i];
         }
-        const double rs_tot = block_sum(rs, red);
-        if (P.want_ke) ke = block_sum(kes, red);
-        r = dsqrt(rs_tot);
+        const double rs_tot = cluster_sum(cl, sh, pt, rs, rb, want_k, kes, &ke);
+        rb ^= 1;
+        r = sqrt(rs_tot);
         ++it;
         if (!isfinite(r)) { status = RVE_NAN; done = true; break; }
         if (r <= thresh) { status = RVE_OK; done = true; break; }
         if (it >= P.max_iter) { status = RVE_MAXITER; done = true; break; }
+        if (P.lead_iters >= 0 ? it >= P.lead_iters : r <= lead_thresh) break;
     }
+    lead = it;
 
-    // ---- phase 2: FP32 increments about an FP64 reference ----
+    // ---- FP32 phase: increments about a double-float reference ----
     if (!done) {
-        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            fv[i] = (float)v0[i]; fv[n + i] = (float)v1[i]; fv[2 * n + i] = (float)v2[i];
-            fa[i] = (float)a0[i]; fa[n + i] = (float)a1[i]; fa[2 * n + i] = (float)a2[i];
+        // x_ref = current positions (Pl holds their FP32 rounding), g_ref = fg,
+        // increments zero. Remote reads of Q0 ended at the last barrier.
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            Q0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            Q1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const float hdtf = (float)hdt, dtf = (float)dt, cf = (float)R.c;
-        bool rebase = true;
-        int since = 0;
+        int b = 0, since = 0, rbp = 0;
+        bool pending = false;
         for (;;) {
-            if (rebase) {
-                // Fold du into u (FP64), stage x = X + u in FP64, g_ref = g(x) in FP64.
-                __syncthreads();
-                if (it > lead) {
-                    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-                        const float4 du = Qq[i];
-                        u0[i] = dadd(u0[i], (double)du.x);
-                        u1[i] = dadd(u1[i], (double)du.y);
-                        u2[i] = dadd(u2[i], (double)du.z);
+            // partial velocity update; displacement increment into buffer b
+            {
+                const float4 *prev = Qb[b ^ 1];
+                float4 *cur = Qb[b];
+                for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+                    const int i = pt.f0 + k;
+                    const float w0 = vh[i] + hdtf * ah[i];
+                    const float w1 = vh[n + i] + hdtf * ah[n + i];
+                    const float w2 = vh[2 * n + i] + hdtf * ah[2 * n + i];
+                    vh[i] = w0; vh[n + i] = w1; vh[2 * n + i] = w2;
+                    const float4 d = prev[k];
+                    cur[k] = make_float4(d.x + dtf * w0, d.y + dtf * w1, d.z + dtf * w2, 0.f);
+                }
+            }
+            cl.sync();
+            if (pending) {
+                // residual of the previous iteration (its state is buffer b^1)
+                const int nw = (blockDim.x + 31) >> 5;
+                double t = 0.0, tk = 0.0;
+                for (int q = 0; q < pt.C; ++q)
+                    for (int w = 0; w < nw; ++w) {
+                        t += sh.red[rbp][q][w];
+                        if (want_k) tk += sh.kred[rbp][q][w];
                     }
-                    __syncthreads();
-                }
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    x0[i] = dadd(X0[i], u0[i]);
-                    x1[i] = dadd(X1[i], u1[i]);
-                    x2[i] = dadd(X2[i], u2[i]);
-                }
-                __syncthreads();
-                for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-                    double g0, g1, g2;
-                    gather_force_fp64(M, rowptr, R.csr0, i, x0, x1, x2, g0, g1, g2);
-                    fg[i] = (float)g0; fg[n + i] = (float)g1; fg[2 * n + i] = (float)g2;
-                }
-                __syncthreads();
-                // Re-stage as FP32 reference positions and zero increments.
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    const float4 xr = make_float4((float)dadd(X0[i], u0[i]), (float)dadd(X1[i], u1[i]),
-                                                  (float)dadd(X2[i], u2[i]), 0.f);
-                    // x0..x2 alias Pq/Qq: read everything of node i above first.
-                    Pq[i] = xr;
-                    Qq[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                __syncthreads();
-                rebase = false;
-                since = 0;
+                if (want_k) ke = tk;
+                r = sqrt(t);
+                if (!isfinite(r)) { status = RVE_NAN; fin = b ^ 1; break; }
+                if (r <= thresh) { status = RVE_OK; fin = b ^ 1; break; }
+                if (it >= P.max_iter) { status = RVE_MAXITER; fin = b ^ 1; break; }
             }
-            // partial velocity update; update displacement increments
-            for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-                float w0 = fv[i] + hdtf * fa[i];
-                float w1 = fv[n + i] + hdtf * fa[n + i];
-                float w2 = fv[2 * n + i] + hdtf * fa[2 * n + i];
-                fv[i] = w0; fv[n + i] = w1; fv[2 * n + i] = w2;
-                float4 du = Qq[i];
-                du.x += dtf * w0; du.y += dtf * w1; du.z += dtf * w2;
-                Qq[i] = du;
-            }
-            __syncthreads();
-            // forces as FP32 increments; damping; residual; accelerations; velocity
+            float4 *cur = Qb[b];
             float rs = 0.f, kes = 0.f;
-            for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-                const float4 pi = Pq[i], qi = Qq[i];
-                float g0 = fg[i], g1 = fg[n + i], g2 = fg[2 * n + i];
-                const int beg = rowptr[i], end = rowptr[i + 1];
-                for (int k = beg; k < end; ++k) {
-                    const int64_t kk = R.csr0 + k;
-                    const int j = M.col[kk];
-                    const float2 ei = M.EAf_invLf[kk];
-                    const float4 pj = Pq[j], qj = Qq[j];
-                    const float r0 = pj.x - pi.x, r1 = pj.y - pi.y, r2 = pj.z - pi.z;
-                    const float e0 = qj.x - qi.x, e1 = qj.y - qi.y, e2 = qj.z - qi.z;
-                    const float lr2 = r0 * r0 + r1 * r1 + r2 * r2;
-                    const float ril = rsqrtf(lr2);
-                    const float lr = lr2 * ril;
-                    const float qref = ei.x * (ei.y - ril);
-                    const float h = 2.f * (r0 * e0 + r1 * e1 + r2 * e2) + (e0 * e0 + e1 * e1 + e2 * e2);
-                    const float rl = rsqrtf(lr2 + h);
-                    const float l = (lr2 + h) * rl;
-                    const float dq = __fdividef(ei.x * h * rl * ril, l + lr);
-                    g0 += qref * e0 + dq * (r0 + e0);
-                    g1 += qref * e1 + dq * (r1 + e1);
-                    g2 += qref * e2 + dq * (r2 + e2);
+            if (since >= K) {
+                // Rebase: fold the increment into the double-float displacement and
+                // stage double-float positions (hi in Pl, lo in buffer b).
+                for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                    const int i = pt.gidx(k);
+                    const float4 d = cur[k];
+                    const float dd[3] = {d.x, d.y, d.z};
+                    df x[3];
+                    for (int c = 0; c < 3; ++c) {
+                        df u = {uh[c * n + i], ul[c * n + i]};
+                        if (k < pt.nfr) {
+                            u = df_add_f(u, dd[c]);
+                            uh[c * n + i] = u.hi; ul[c * n + i] = u.lo;
+                        }
+                        x[c] = df_add({Xh[c * n + i], Xl[c * n + i]}, u);
+                    }
+                    Pl[k] = make_float4(x[0].hi, x[1].hi, x[2].hi, 0.f);
+                    cur[k] = make_float4(x[0].lo, x[1].lo, x[2].lo, 0.f);
                 }
-                const float im = inv_m[i];
-                float w0 = fv[i], w1 = fv[n + i], w2 = fv[2 * n + i];
-                const float aa0 = g0 * im - cf * w0;
-                const float aa1 = g1 * im - cf * w1;
-                const float aa2 = g2 * im - cf * w2;
-                w0 += hdtf * aa0; w1 += hdtf * aa1; w2 += hdtf * aa2;
-                fa[i] = aa0; fa[n + i] = aa1; fa[2 * n + i] = aa2;
-                fv[i] = w0; fv[n + i] = w1; fv[2 * n + i] = w2;
-                rs += g0 * g0 + g1 * g1 + g2 * g2;
-                if (P.want_ke) kes += (w0 * w0 + w1 * w1 + w2 * w2) * (0.5f / im);
+                cl.sync();
+                for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+                    const int i = pt.f0 + k;
+                    df g[3];
+                    gather_df(M, R, rowptr, sh, pt, k, Pl, cur, b, g[0], g[1], g[2]);
+                    fg[i] = g[0].hi; fg[n + i] = g[1].hi; fg[2 * n + i] = g[2].hi;
+                }
+                cl.sync();
+                for (int k = threadIdx.x; k < m; k += blockDim.x) cur[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                // accelerations and velocities from the reference force
+                for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+                    const int i = pt.f0 + k;
+                    const float im = imh[i];
+                    float vv = 0.f;
+                    for (int c = 0; c < 3; ++c) {
+                        const float g = fg[c * n + i];
+                        float w = vh[c * n + i];
+                        const float a = g * im - cf * w;
+                        w += hdtf * a;
+                        ah[c * n + i] = a;
+                        vh[c * n + i] = w;
+                        rs += g * g;
+                        vv += w * w;
+                    }
+                    if (want_k) kes += 0.5f * vv / im;
+                }
+                since = 0;
+            } else {
+                for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+                    const int i = pt.f0 + k;
+                    const float4 pi = Pl[k], qi = cur[k];
+                    float g0 = fg[i], g1 = fg[n + i], g2 = fg[2 * n + i];
+                    const int beg = rowptr[i], end = rowptr[i + 1];
+                    for (int e = beg; e < end; ++e) {
+                        const int64_t kk = R.csr0 + e;
+                        const int cp = M.col_part[kk];
+                        const int rr = cp >> 16, loc = cp & 0xffff;
+                        const float2 ei = M.eaf[kk];
+                        const float4 pj = rr == pt.me ? Pl[loc] : sh.P[rr][loc];
+                        const float4 qj = rr == pt.me ? cur[loc] : sh.Q[b][rr][loc];
+                        const float r0 = pj.x - pi.x, r1 = pj.y - pi.y, r2 = pj.z - pi.z;
+                        const float e0 = qj.x - qi.x, e1 = qj.y - qi.y, e2 = qj.z - qi.z;
+                        const float lr2 = r0 * r0 + r1 * r1 + r2 * r2;
+                        const float ril = rsqrtf(lr2);
+                        const float lr = lr2 * ril;
+                        const float qref = ei.x * (ei.y - ril);
+                        const float h = 2.f * (r0 * e0 + r1 * e1 + r2 * e2) + (e0 * e0 + e1 * e1 + e2 * e2);
+                        const float rl = rsqrtf(lr2 + h);
+                        const float l = (lr2 + h) * rl;
+                        const float dq = __fdividef(ei.x * h * rl * ril, l + lr);
+                        g0 += qref * e0 + dq * (r0 + e0);
+                        g1 += qref * e1 + dq * (r1 + e1);
+                        g2 += qref * e2 + dq * (r2 + e2);
+                    }
+                    const float im = imh[i];
+                    float w0 = vh[i], w1 = vh[n + i], w2 = vh[2 * n + i];
+                    const float a0 = g0 * im - cf * w0;
+                    const float a1 = g1 * im - cf * w1;
+                    const float a2 = g2 * im - cf * w2;
+                    w0 += hdtf * a0; w1 += hdtf * a1; w2 += hdtf * a2;
+                    ah[i] = a0; ah[n + i] = a1; ah[2 * n + i] = a2;
+                    vh[i] = w0; vh[n + i] = w1; vh[2 * n + i] = w2;
+                    rs += g0 * g0 + g1 * g1 + g2 * g2;
+                    if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
+                }
             }
-            const double rs_tot = block_sum_f(rs, red);
-            if (P.want_ke) ke = block_sum_f(kes, red);
-            r = sqrt(rs_tot);
+            // publish this iteration's partials; tested after the next barrier
+            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+            if (want_k)
+                for (int o = 16; o > 0; o >>= 1) kes += __shfl_xor_sync(0xffffffffu, kes, o);
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (lane < pt.C) {
+                sh.redp[lane][(rb * kMaxParts + pt.me) * kMaxWarps + warp] = (double)rs;
+                if (want_k) sh.kredp[lane][(rb * kMaxParts + pt.me) * kMaxWarps + warp] = (double)kes;
+            }
+            rbp = rb;
+            rb ^= 1;
+            pending = true;
             ++it;
             ++since;
-            if (!isfinite(r)) { status = RVE_NAN; break; }
-            if (r <= thresh) { status = RVE_OK; break; }
-            if (it >= P.max_iter) { status = RVE_MAXITER; break; }
-            if (since >= K) rebase = true;
+            b ^= 1;
         }
-        // Final displacement u = u_ref + du (FP64) and FP64 positions for the stress.
-        for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-            const float4 du = Qq[i];
-            u0[i] = dadd(u0[i], (double)du.x);
-            u1[i] = dadd(u1[i], (double)du.y);
-            u2[i] = dadd(u2[i], (double)du.z);
+    }
+
+    // ---- final displacement (FP64 output) and positions for the stress ----
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int i = pt.gidx(k);
+        float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (fin >= 0 && k < pt.nfr) d = Qb[fin][k];
+        const float dd[3] = {d.x, d.y, d.z};
+        double *uo[3] = {S.u0 + n0, S.u1 + n0, S.u2 + n0};
+        const double *Xd[3] = {M.X0 + n0, M.X1 + n0, M.X2 + n0};
+        for (int c = 0; c < 3; ++c) {
+            df u = {uh[c * n + i], ul[c * n + i]};
+            if (fin >= 0 && k < pt.nfr) u = df_add_f(u, dd[c]);
+            const double ud = df_to_double(u);
+            uo[c][i] = ud;
+            xg[c * n + i] = dadd(Xd[c][i], ud);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            x0[i] = dadd(X0[i], u0[i]);
-            x1[i] = dadd(X1[i], u1[i]);
-            x2[i] = dadd(X2[i], u2[i]);
+    }
+    cl.sync();
+    // stress: elements split across the cluster, partials reduced on rank 0
+    double s[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s[k] = 0.0;
+    {
+        const double *x0 = xg, *x1 = xg + n, *x2 = xg + 2 * n;
+        for (int e = pt.me * blockDim.x + threadIdx.x; e < R.n_elems; e += pt.C * blockDim.x) {
+            const int64_t ee = R.elem0 + e;
+            const int a = M.el_a[ee], bb = M.el_b[ee];
+            double d[3] = {dsub(x0[bb], x0[a]), dsub(x1[bb], x1[a]), dsub(x2[bb], x2[a])};
+            const double l = dsqrt(dadd(dadd(dmul(d[0], d[0]), dmul(d[1], d[1])), dmul(d[2], d[2])));
+            const double q = ddiv(dmul(M.el_EA[ee], dsub(ddiv(l, M.el_L[ee]), 1.0)), l);
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) s[3 * rr + c] = dadd(s[3 * rr + c], dmul(dmul(q, d[rr]), d[c]));
+        }
+    }
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double v = s[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sh.wsum[warp][k] = v;
         }
     }
     __syncthreads();
-    rve_stress(M, R, F, x0, x1, x2, O.sigma + 9 * (int64_t)p, red);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 9) {
+        double t = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += sh.wsum[w][threadIdx.x];
+        sh.sigp[pt.me * 9 + threadIdx.x] = t;
+    }
+    cl.sync();
+    if (pt.me == 0 && threadIdx.x < 9) {
+        double t = 0.0;
+        for (int q = 0; q < pt.C; ++q) t += sh.sig[q][threadIdx.x];
+        O.sigma[9 * (int64_t)p + threadIdx.x] = ddiv(t, dmul(det3(F), R.V0));
+    }
+    if (pt.me == 0 && threadIdx.x == 0) {
         O.iters[p] = it;
         O.rel_res[p] = f_ref > 0.0 ? r / f_ref : (r > 0.0 ? INFINITY : 0.0);
         O.status[p] = status;
         O.f_ref[p] = f_ref;
         O.ke[p] = ke;
+        O.lead[p] = lead;
     }
-    __syncthreads();
+    cl.sync();
 }
 
-template <bool SM>
+}  // namespace
+
 __global__ void __launch_bounds__(512) dr_mixed_kernel(DevMesh M, DevState S, DevResults O,
-                                                        SolveParams P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
-    __shared__ int s_item;
+                                                       SolveParams P, int part_cap) {
+    extern __shared__ __align__(16) float4 dsm[];
+    __shared__ MixedShared sh;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    float4 *Pl = dsm, *Q0 = dsm + part_cap, *Q1 = dsm + 2 * part_cap;
+    if ((int)threadIdx.x < C) {
+        const int r = threadIdx.x;
+        sh.P[r] = cl.map_shared_rank(Pl, r);
+        sh.Q[0][r] = cl.map_shared_rank(Q0, r);
+        sh.Q[1][r] = cl.map_shared_rank(Q1, r);
+        sh.redp[r] = cl.map_shared_rank(&sh.red[0][0][0], r);
+        sh.kredp[r] = cl.map_shared_rank(&sh.kred[0][0][0], r);
+    }
+    if (threadIdx.x == 0) sh.sigp = cl.map_shared_rank(&sh.sig[0][0], 0);
+    int rb = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(P.counter, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
+        if (cl.block_rank() == 0 && threadIdx.x == 0) sh.item = atomicAdd(P.counter, 1);
+        cl.sync();
+        const int item = *cl.map_shared_rank(&sh.item, 0);
+        cl.sync();
         if (item >= P.queue_len) return;
-        solve_rve_mixed<SM>(M, S, O, P, P.queue[item], smem_raw, red);
+        solve_rve_mixed(cl, sh, M, S, O, P, P.queue[item], Pl, Q0, Q1, rb);
     }
 }
+
+namespace {
+cudaLaunchConfig_t mixed_config(int clusters, int parts, int block, size_t smem,
+                                cudaLaunchAttribute *attr, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(clusters * parts, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = parts;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+}  // namespace
 
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
-                    int grid, int block, size_t smem, void *stream) {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (p.smem_positions) {
-        cudaFuncSetAttribute(dr_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        dr_mixed_kernel<true><<<grid, block, smem, st>>>(m, s, r, p);
-    } else {
-        dr_mixed_kernel<false><<<grid, block, 0, st>>>(m, s, r, p);
-    }
+                    int clusters, int parts, int block, size_t smem, void *stream) {
+    cudaFuncSetAttribute(dr_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(dr_mixed_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg =
+        mixed_config(clusters, parts, block, smem, attr, static_cast<cudaStream_t>(stream));
+    const int part_cap = (int)(smem / (3 * sizeof(float4)));
+    cudaError_t e = cudaLaunchKernelEx(&cfg, dr_mixed_kernel, m, s, r, p, part_cap);
+    if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 
-int occupancy_dr_mixed(int smem_positions, int block, size_t smem) {
+int occupancy_dr_mixed(int parts, int block, size_t smem) {
+    cudaFuncSetAttribute(dr_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(dr_mixed_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = mixed_config(parts * 64, parts, block, smem, attr, nullptr);
     int n = 0;
-    if (smem_positions) {
-        cudaFuncSetAttribute(dr_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dr_mixed_kernel<true>, block, smem);
-    } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dr_mixed_kernel<false>, block, 0);
+    if (cudaOccupancyMaxActiveClusters(&n, dr_mixed_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
     }
     return n;
 }

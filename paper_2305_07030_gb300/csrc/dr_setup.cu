@@ -17,14 +17,23 @@ __global__ void k_elem_lengths(int64_t n_el, const int64_t *ga, const int64_t *g
     }
 }
 
-// Per CSR entry: the element's L, and (EA, 1/L) rounded to FP32.
+__device__ __forceinline__ void split_df(double d, float &hi, float &lo) {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+}
+
+// Per CSR entry: the element's L, and (EA, 1/L) as double-float pairs.
 __global__ void k_csr_fill(int64_t n_csr, const int64_t *elem_of, const double *el_L,
-                           const double *EA_csr, double *L_csr, float2 *eaf) {
+                           const double *EA_csr, double *L_csr, float2 *eaf, float2 *eaf_lo) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_csr;
          k += (int64_t)gridDim.x * blockDim.x) {
         const double L = el_L[elem_of[k]];
         L_csr[k] = L;
-        eaf[k] = make_float2((float)EA_csr[k], (float)(1.0 / L));
+        float eh, el, ih, il;
+        split_df(EA_csr[k], eh, el);
+        split_df(1.0 / L, ih, il);
+        eaf[k] = make_float2(eh, ih);
+        eaf_lo[k] = make_float2(el, il);
     }
 }
 
@@ -33,7 +42,8 @@ __global__ void k_csr_fill(int64_t n_csr, const int64_t *elem_of, const double *
 // min_e L_e sqrt(rho A_e / EA_e).
 __global__ void k_mass_dt(RveDesc *rve, const int32_t *rowptr, const double *EA_csr,
                           const double *L_csr, const double *el_EA, const double *el_L,
-                          double *mass, float *inv_mass_f) {
+                          const double *X0, const double *X1, const double *X2, double *mass,
+                          float *imh, float *iml, float *Xh, float *Xl) {
     __shared__ double red[32];
     RveDesc &R = rve[blockIdx.x];
     const int32_t *rp = rowptr + R.rp0;
@@ -46,7 +56,14 @@ __global__ void k_mass_dt(RveDesc *rve, const int32_t *rowptr, const double *EA_
             m = dadd(m, dmul(0.5, dmul(rhoA, L)));
         }
         mass[R.node0 + i] = m;
-        inv_mass_f[R.node0 + i] = m > 0.0 ? (float)(1.0 / m) : 0.f;
+        float h = 0.f, l = 0.f;
+        if (m > 0.0) split_df(1.0 / m, h, l);
+        imh[R.node0 + i] = h;
+        iml[R.node0 + i] = l;
+        // reference coordinates as double-float, per-RVE [3][n] blocks
+        const double X[3] = {X0[R.node0 + i], X1[R.node0 + i], X2[R.node0 + i]};
+        for (int c = 0; c < 3; ++c)
+            split_df(X[c], Xh[3 * R.node0 + c * R.n_nodes + i], Xl[3 * R.node0 + c * R.n_nodes + i]);
     }
     double tmin = INFINITY;
     for (int e = threadIdx.x; e < R.n_elems; e += blockDim.x) {
@@ -74,7 +91,9 @@ int launch_setup(int32_t n_rve, int64_t n_el, int64_t n_csr, RveDesc *rve,
                  const int64_t *ga, const int64_t *gb, const double *X0, const double *X1,
                  const double *X2, const int64_t *elem_of, const double *EA_csr,
                  const double *el_EA, const int32_t *rowptr, double *el_L, double *L_csr,
-                 float2 *eaf, double *mass, float *inv_mass_f, void *stream) {
+                 float2 *eaf, float2 *eaf_lo, double *mass, float *imh, float *iml,
+                 float *Xh, float *Xl, int64_t n_nodes, void *stream) {
+    (void)n_nodes;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n_el > 0) {
         const int g = (int)((n_el + 255) / 256 < 65535 ? (n_el + 255) / 256 : 65535);
@@ -82,9 +101,10 @@ int launch_setup(int32_t n_rve, int64_t n_el, int64_t n_csr, RveDesc *rve,
     }
     if (n_csr > 0) {
         const int g = (int)((n_csr + 255) / 256 < 65535 ? (n_csr + 255) / 256 : 65535);
-        k_csr_fill<<<g, 256, 0, st>>>(n_csr, elem_of, el_L, EA_csr, L_csr, eaf);
+        k_csr_fill<<<g, 256, 0, st>>>(n_csr, elem_of, el_L, EA_csr, L_csr, eaf, eaf_lo);
     }
-    k_mass_dt<<<n_rve, 256, 0, st>>>(rve, rowptr, EA_csr, L_csr, el_EA, el_L, mass, inv_mass_f);
+    k_mass_dt<<<n_rve, 256, 0, st>>>(rve, rowptr, EA_csr, L_csr, el_EA, el_L, X0, X1, X2, mass,
+                                     imh, iml, Xh, Xl);
     return (int)cudaGetLastError();
 }
 

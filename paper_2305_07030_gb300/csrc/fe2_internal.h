@@ -4,18 +4,26 @@
 // vector plus value vectors holding every sub-problem of a rank contiguously,
 // Section III), re-laid out for the GPU:
 //   * nodes of RVE p occupy [node0, node0 + n_nodes) of every node array, free
-//     nodes first (the paper's free/fixed reordering, Section III), free nodes
-//     sorted by degree so that a warp's gathers have equal trip counts;
+//     nodes first (the paper's free/fixed reordering, Section III);
+//   * an RVE is split spatially (recursive coordinate bisection) into
+//     n_parts parts, one per CTA of the thread-block cluster that solves it in
+//     mixed precision. Free nodes are ordered part by part (by degree within a
+//     part), then fixed nodes part by part, so part r owns the free range
+//     [part_f[r], part_f[r+1]) and the fixed range n_free + [part_g[r], part_g[r+1]);
 //   * each node has a CSR row of its incident elements (node-centric, so the
 //     force gather needs no atomics), ordered by the neighbour's ORIGINAL id:
-//     this is the order in which a serial element scatter over lexicographic
-//     (a < b) elements touches the node, which keeps FP64 sums bit-identical;
+//     the order in which a serial element scatter over lexicographic (a < b)
+//     elements touches the node, which keeps FP64 sums bit-identical. `col`
+//     holds the neighbour's RVE-local index, `col_part` the same neighbour as
+//     (owning part << 16 | index inside that part's shared-memory arrays);
 //   * structure-of-arrays per component for coalesced access.
 #pragma once
-#include <stdint.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace fe2 {
+
+constexpr int kMaxParts = 16;  // largest (non-portable) thread-block cluster
 
 struct RveDesc {
     int64_t node0;    // first node (permuted, global index)
@@ -25,25 +33,30 @@ struct RveDesc {
     int32_t n_nodes;
     int32_t n_free;
     int32_t n_elems;
-    int32_t max_deg;
+    int32_t n_parts;  // cluster size of the mixed solver for this RVE
     double dtc;       // critical time step (safety factor not applied)
     double c;         // damping coefficient
     double V0;        // reference volume
-    double pad;
+    int32_t part_max; // largest part (nodes), sizes the shared memory
+    int32_t pad;
 };
 
 // Read-only, create-time arrays.
 struct DevMesh {
     const RveDesc *rve;
     const double *X0, *X1, *X2;   // reference coordinates (permuted)
+    const float *Xh, *Xl;         // reference coordinates as double-float, [3][N]
     const double *mass;           // lumped nodal mass
-    const float *inv_mass_f;      // 1/m in FP32
+    const float *imh, *iml;       // 1/m as double-float
     const int32_t *rowptr;        // per RVE n_nodes + 1 entries
-    const int32_t *col;           // neighbour (local permuted id)
+    const int32_t *col;           // neighbour (RVE-local permuted id)
+    const int32_t *col_part;      // neighbour as (part << 16 | index in part)
+    const int32_t *part_off;      // per RVE 2*(kMaxParts+1): part_f[], part_g[]
     const double *EA;             // per CSR entry
     const double *L;              // per CSR entry
-    const float2 *EAf_invLf;      // per CSR entry: (EA, 1/L) in FP32
-    const int32_t *el_a, *el_b;   // stress elements (local permuted ids)
+    const float2 *eaf;            // per CSR entry: (EA, 1/L) double-float high parts
+    const float2 *eaf_lo;         // per CSR entry: low parts
+    const int32_t *el_a, *el_b;   // stress elements (RVE-local permuted ids)
     const double *el_EA, *el_L;
 };
 
@@ -52,9 +65,11 @@ struct DevState {
     double *u0, *u1, *u2;         // displacement (output of every mode)
     double *v0, *v1, *v2;         // FP64 velocity
     double *a0, *a1, *a2;         // FP64 acceleration
-    float *fv, *fa, *fg;          // MIXED: FP32 velocity, acceleration, g_ref (3*N each, SoA)
-    double *xg;                   // 3*N global position scratch (RVEs too big for SMEM)
-    float4 *pg;                   // 2*N float4 scratch (mixed positions, big RVEs)
+    float *uh, *ul;               // MIXED: displacement, double-float [3][N]
+    float *vh, *vl;               // MIXED: velocity (lead: double-float; FP32 phase: vh)
+    float *ah, *al;               // MIXED: acceleration (same convention)
+    float *fg;                    // MIXED: reference force g_ref, FP32 [3][N]
+    double *xg;                   // [3][N] FP64 positions scratch
 };
 
 struct DevResults {
@@ -64,6 +79,7 @@ struct DevResults {
     int32_t *status;
     double *f_ref;
     double *ke;
+    int64_t *lead;    // MIXED: iterations run in the double-float lead
 };
 
 struct SolveParams {
@@ -73,12 +89,13 @@ struct SolveParams {
     double alpha;
     int init;
     int want_ke;
-    int64_t lead_iters;   // < 0: default rule
+    int64_t lead_iters;   // < 0: lead until the relative residual <= lead_tol
+    double lead_tol;
     int rebase_every;
     const int32_t *queue; // RVE ids in scheduling order
     int32_t queue_len;
     int32_t *counter;     // work-queue head (zeroed before the launch)
-    int smem_positions;   // 1: positions staged in shared memory
+    int smem_positions;   // FP64 kernel: 1 = positions staged in shared memory
 };
 
 enum { RVE_OK = 0, RVE_MAXITER = 1, RVE_NAN = 2, RVE_PENDING = 3 };
@@ -88,11 +105,18 @@ int launch_setup(int32_t n_rve, int64_t n_el, int64_t n_csr, RveDesc *rve,
                  const int64_t *ga, const int64_t *gb, const double *X0, const double *X1,
                  const double *X2, const int64_t *elem_of, const double *EA_csr,
                  const double *el_EA, const int32_t *rowptr, double *el_L, double *L_csr,
-                 float2 *eaf, double *mass, float *inv_mass_f, void *stream);
+                 float2 *eaf, float2 *eaf_lo, double *mass, float *imh, float *iml,
+                 float *Xh, float *Xl, int64_t n_nodes, void *stream);
 int launch_dr_fp64(const DevMesh &m, const DevState &s, const DevResults &r,
                    const SolveParams &p, int grid, int block, size_t smem, void *stream);
+// Mixed solver: one thread-block cluster of `parts` CTAs per RVE.
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r,
-                    const SolveParams &p, int grid, int block, size_t smem, void *stream);
+                    const SolveParams &p, int clusters, int parts, int block, size_t smem,
+                    void *stream);
+// Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.
+int occupancy_dr_fp64(int smem_positions, int block, size_t smem);
+int occupancy_dr_mixed(int parts, int block, size_t smem);
+
 // Naive comparator: scratch sized for the largest RVE, and one RVE's solve.
 struct NaiveScratch {
     double *x, *g, *acc;  // 3*n_max, 3*n_max, 16
@@ -101,8 +125,5 @@ int naive_solve_rve(const RveDesc &R, const DevMesh &M, const DevState &S, const
                     const double *F_dev, const NaiveScratch &W, double tol, int64_t max_iter,
                     double alpha, int init, int p, cudaStream_t st, int64_t *iters_out,
                     double *rel_out, int *status_out);
-// Resident CTAs per SM for a launch shape.
-int occupancy_dr_fp64(int smem_positions, int block, size_t smem);
-int occupancy_dr_mixed(int smem_positions, int block, size_t smem);
 
 }  // namespace fe2

@@ -1,14 +1,17 @@
 // Host runtime behind the C ABI of include/fe2.h: input validation, packing
-// into the device layout of fe2_internal.h, size classes, the cost-ordered work
-// queue, persistent launches, and result readback.
+// into the device layout of fe2_internal.h (free/fixed reordering, spatial
+// parts per cluster CTA, node-centric CSR), size classes, the cost-ordered
+// work queue, persistent launches and result readback.
 //
 // Algorithm 1 steps 1-3 (load mesh, build connectivity, transfer to the GPU)
-// happen here once per batch; steps 4 onward run in the kernels.
+// happen here once per batch; the mass matrix and time step are computed by
+// create-time kernels, and every solver step runs in the solve kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -54,11 +57,19 @@ struct DevBuf {
 
 // One size class: RVEs solved by one persistent launch.
 struct SizeClass {
-    int smem_positions;       // positions in shared memory
-    size_t smem_bytes;        // dynamic shared memory per CTA
+    int parts = 1;              // mixed: cluster size
+    int smem_positions = 1;     // FP64: positions in shared memory
+    size_t smem_bytes = 0;      // dynamic shared memory per CTA
+    int part_max = 0;           // mixed: largest part (nodes)
+    int free_max = 0;           // mixed: most free nodes in one part
     std::vector<int32_t> rves;  // in scheduling order
-    int32_t queue_off;        // offset of its queue in the device queue buffer
+    int32_t queue_off = 0;      // offset of its queue in the device queue buffer
 };
+
+int env_int(const char *name, int dflt) {
+    const char *v = std::getenv(name);
+    return v && *v ? std::atoi(v) : dflt;
+}
 
 }  // namespace
 
@@ -70,33 +81,31 @@ struct fe2_batch {
     size_t smem_optin = 0;
     std::vector<RveDesc> rve;             // host copy
     std::vector<int64_t> perm_to_orig;    // permuted global -> caller global node
-    std::vector<int32_t> n_nodes_of;      // per RVE
-    std::vector<uint8_t> is_fixed_perm;   // permuted
+    std::vector<int32_t> part_free_max;   // per RVE, most free nodes in one part
 
     // device arrays
     DevBuf<RveDesc> d_rve;
     DevBuf<double> d_X, d_mass, d_EA_csr, d_L_csr, d_el_EA, d_el_L;
-    DevBuf<float> d_inv_mass_f;
-    DevBuf<int32_t> d_rowptr, d_col, d_el_a, d_el_b;
-    DevBuf<float2> d_eaf;
+    DevBuf<float> d_Xh, d_Xl, d_imh, d_iml;
+    DevBuf<int32_t> d_rowptr, d_col, d_col_part, d_part_off, d_el_a, d_el_b;
+    DevBuf<float2> d_eaf, d_eaf_lo;
     DevBuf<double> d_u, d_v, d_a, d_xg;
-    DevBuf<float> d_fv, d_fa, d_fg;
-    DevBuf<float4> d_pg;
+    DevBuf<float> d_uh, d_ul, d_vh, d_vl, d_ah, d_al, d_fg;
     DevBuf<double> d_F, d_sigma, d_rel, d_fref, d_ke;
-    DevBuf<int64_t> d_iters;
+    DevBuf<int64_t> d_iters, d_lead;
     DevBuf<int32_t> d_status, d_queue, d_counters;
+    DevBuf<double> d_naive;               // naive comparator scratch (first use)
 
     std::vector<SizeClass> classes_fp64, classes_mixed;
     bool solved = false;
     int32_t last_launches = 0;
-    int32_t last_timed = 0;            // persistent launches bracketed by tev
+    int32_t last_timed = 0;               // persistent launches bracketed by tev
     cudaStream_t last_stream = nullptr;
-    std::vector<cudaStream_t> side;  // forked streams for concurrent classes
+    std::vector<cudaStream_t> side;       // forked streams for concurrent classes
     std::vector<cudaEvent_t> ev;
-    std::vector<cudaEvent_t> tev;      // timing events around each class launch
-    DevBuf<double> d_naive;           // naive comparator scratch (allocated on first use)
-    double *h_F = nullptr;             // pinned staging for F
-    cudaEvent_t ev_F = nullptr;        // completion of the last F upload
+    std::vector<cudaEvent_t> tev;         // timing events around each class launch
+    double *h_F = nullptr;                // pinned staging for F
+    cudaEvent_t ev_F = nullptr;           // completion of the last F upload
 
     DevMesh mesh() const {
         DevMesh m;
@@ -104,13 +113,19 @@ struct fe2_batch {
         m.X0 = d_X.p;
         m.X1 = d_X.p + n_nodes;
         m.X2 = d_X.p + 2 * n_nodes;
+        m.Xh = d_Xh.p;
+        m.Xl = d_Xl.p;
         m.mass = d_mass.p;
-        m.inv_mass_f = d_inv_mass_f.p;
+        m.imh = d_imh.p;
+        m.iml = d_iml.p;
         m.rowptr = d_rowptr.p;
         m.col = d_col.p;
+        m.col_part = d_col_part.p;
+        m.part_off = d_part_off.p;
         m.EA = d_EA_csr.p;
         m.L = d_L_csr.p;
-        m.EAf_invLf = d_eaf.p;
+        m.eaf = d_eaf.p;
+        m.eaf_lo = d_eaf_lo.p;
         m.el_a = d_el_a.p;
         m.el_b = d_el_b.p;
         m.el_EA = d_el_EA.p;
@@ -122,25 +137,27 @@ struct fe2_batch {
         s.u0 = d_u.p; s.u1 = d_u.p + n_nodes; s.u2 = d_u.p + 2 * n_nodes;
         s.v0 = d_v.p; s.v1 = d_v.p + n_nodes; s.v2 = d_v.p + 2 * n_nodes;
         s.a0 = d_a.p; s.a1 = d_a.p + n_nodes; s.a2 = d_a.p + 2 * n_nodes;
-        s.fv = d_fv.p; s.fa = d_fa.p; s.fg = d_fg.p;
+        s.uh = d_uh.p; s.ul = d_ul.p; s.vh = d_vh.p; s.vl = d_vl.p;
+        s.ah = d_ah.p; s.al = d_al.p; s.fg = d_fg.p;
         s.xg = d_xg.p;
-        s.pg = d_pg.p;
         return s;
     }
     DevResults results() const {
         DevResults r;
         r.sigma = d_sigma.p; r.iters = d_iters.p; r.rel_res = d_rel.p;
-        r.status = d_status.p; r.f_ref = d_fref.p; r.ke = d_ke.p;
+        r.status = d_status.p; r.f_ref = d_fref.p; r.ke = d_ke.p; r.lead = d_lead.p;
         return r;
     }
     void release() {
         d_rve.release(); d_X.release(); d_mass.release(); d_EA_csr.release(); d_L_csr.release();
-        d_el_EA.release(); d_el_L.release(); d_inv_mass_f.release(); d_rowptr.release();
-        d_col.release(); d_el_a.release(); d_el_b.release(); d_eaf.release(); d_u.release();
-        d_v.release(); d_a.release(); d_xg.release(); d_fv.release(); d_fa.release();
-        d_fg.release(); d_pg.release(); d_F.release(); d_sigma.release(); d_rel.release();
-        d_fref.release(); d_ke.release(); d_iters.release(); d_status.release();
-        d_queue.release(); d_counters.release(); d_naive.release();
+        d_el_EA.release(); d_el_L.release(); d_Xh.release(); d_Xl.release(); d_imh.release();
+        d_iml.release(); d_rowptr.release(); d_col.release(); d_col_part.release();
+        d_part_off.release(); d_el_a.release(); d_el_b.release(); d_eaf.release();
+        d_eaf_lo.release(); d_u.release(); d_v.release(); d_a.release(); d_xg.release();
+        d_uh.release(); d_ul.release(); d_vh.release(); d_vl.release(); d_ah.release();
+        d_al.release(); d_fg.release(); d_F.release(); d_sigma.release(); d_rel.release();
+        d_fref.release(); d_ke.release(); d_iters.release(); d_lead.release();
+        d_status.release(); d_queue.release(); d_counters.release(); d_naive.release();
         if (h_F) cudaFreeHost(h_F);
         h_F = nullptr;
         if (ev_F) cudaEventDestroy(ev_F);
@@ -168,6 +185,7 @@ void fe2_opts_default(fe2_opts *o) {
     o->block_threads = 0;
     o->lead_iters = -1;
     o->rebase_every = 0;
+    o->lead_tol = 1e-3;
 }
 
 const char *fe2_last_error(void) { return g_err.c_str(); }
@@ -178,41 +196,87 @@ namespace {
 
 bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
-// Shared-memory bytes a CTA needs to stage one RVE's positions.
-size_t smem_need(int precision, int n) {
-    return precision == FE2_PREC_FP64 ? (size_t)24 * n : (size_t)32 * n;
+// Number of cluster CTAs for an RVE of n nodes in the mixed solver: a power
+// of two with about `target` nodes per CTA, enough parts for the staged
+// positions (48 B per node) to fit in shared memory, at most 16.
+int choose_parts(int n, int target, size_t smem_cap) {
+    int C = 1;
+    while (C < kMaxParts && ((n + C - 1) / C > target || (size_t)48 * ((n + C - 1) / C + 64) > smem_cap))
+        C *= 2;
+    return C;
 }
 
-// Bucket RVEs into classes by staged footprint so that small RVEs are not
-// limited by the occupancy of the largest; too-large RVEs stage in L2 scratch.
+// Recursive coordinate bisection of `ids` into `parts` (a power of two) sets.
+void rcb(std::vector<int> ids, int parts, const double *X, int64_t base,
+         std::vector<std::vector<int>> &out) {
+    if (parts == 1) {
+        out.push_back(std::move(ids));
+        return;
+    }
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i : ids)
+        for (int c = 0; c < 3; ++c) {
+            const double v = X[3 * (base + i) + c];
+            lo[c] = std::min(lo[c], v);
+            hi[c] = std::max(hi[c], v);
+        }
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+        if (hi[c] - lo[c] > hi[ax] - lo[ax]) ax = c;
+    std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) {
+        const double va = X[3 * (base + a) + ax], vb = X[3 * (base + b) + ax];
+        return va < vb || (va == vb && a < b);
+    });
+    const size_t half = ids.size() / 2;
+    rcb(std::vector<int>(ids.begin(), ids.begin() + half), parts / 2, X, base, out);
+    rcb(std::vector<int>(ids.begin() + half, ids.end()), parts / 2, X, base, out);
+}
+
+// Bucket RVEs into launch classes. FP64: by staged footprint (24 B/node), so
+// small RVEs are not limited by the occupancy of the largest; RVEs too big for
+// shared memory stage in L2 scratch. Mixed: by cluster size.
 void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
     out.clear();
-    const size_t cap = b->smem_optin - 1024;  // leave room for static shared memory
-    const size_t bounds[] = {16u << 10, 32u << 10, 56u << 10, 112u << 10, cap};
-    std::vector<SizeClass> cls(6);
-    for (int c = 0; c < 5; ++c) { cls[c].smem_positions = 1; cls[c].smem_bytes = 0; }
-    cls[5].smem_positions = 0;
-    cls[5].smem_bytes = 0;
-    // cost-ordered (largest first): longest-processing-time scheduling
     std::vector<int32_t> order(b->n_rve);
     std::iota(order.begin(), order.end(), 0);
+    // longest-processing-time first: largest RVEs lead the queue
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
         return b->rve[x].n_free > b->rve[y].n_free;
     });
-    for (int32_t p : order) {
-        const size_t need = smem_need(precision, b->rve[p].n_nodes);
-        int c = 5;
-        for (int k = 0; k < 5; ++k)
-            if (need <= bounds[k] && need <= cap) { c = k; break; }
-        cls[c].rves.push_back(p);
-        if (c < 5) cls[c].smem_bytes = std::max(cls[c].smem_bytes, need);
+    const size_t cap = b->smem_optin - 16384;  // room for static shared memory
+    if (precision == FE2_PREC_FP64) {
+        const size_t bounds[] = {16u << 10, 32u << 10, 56u << 10, 112u << 10, cap};
+        std::vector<SizeClass> cls(6);
+        cls[5].smem_positions = 0;
+        for (int32_t p : order) {
+            const size_t need = (size_t)24 * b->rve[p].n_nodes;
+            int c = 5;
+            for (int k = 0; k < 5; ++k)
+                if (need <= bounds[k] && need <= cap) { c = k; break; }
+            cls[c].rves.push_back(p);
+            if (c < 5) cls[c].smem_bytes = std::max(cls[c].smem_bytes, need);
+        }
+        for (auto &c : cls)
+            if (!c.rves.empty()) out.push_back(c);
+    } else {
+        std::vector<SizeClass> cls(5);  // parts 1, 2, 4, 8, 16
+        for (int k = 0; k < 5; ++k) cls[k].parts = 1 << k;
+        for (int32_t p : order) {
+            int k = 0;
+            while ((1 << k) < b->rve[p].n_parts) ++k;
+            SizeClass &c = cls[k];
+            c.rves.push_back(p);
+            c.part_max = std::max(c.part_max, b->rve[p].part_max);
+            c.free_max = std::max(c.free_max, b->part_free_max[p]);
+            c.smem_bytes = (size_t)48 * c.part_max;
+        }
+        for (auto &c : cls)
+            if (!c.rves.empty()) out.push_back(c);
     }
     int32_t off = 0;
-    for (auto &c : cls) {
-        if (c.rves.empty()) continue;
+    for (auto &c : out) {
         c.queue_off = off;
         off += (int32_t)c.rves.size();
-        out.push_back(c);
     }
 }
 
@@ -229,11 +293,13 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     if (node_off[0] != 0 || elem_off[0] != 0) return fail(FE2_EINVAL, "offsets must start at 0");
     for (int32_t p = 0; p < n_rve; ++p) {
         if (node_off[p + 1] <= node_off[p]) return fail(FE2_EINVAL, "RVE " + std::to_string(p) + " has no nodes");
-        if (node_off[p + 1] - node_off[p] > (1 << 30)) return fail(FE2_EINVAL, "RVE too large");
+        if (node_off[p + 1] - node_off[p] > (1 << 20))
+            return fail(FE2_EINVAL, "RVE " + std::to_string(p) + " has more than 2^20 nodes");
         if (elem_off[p + 1] < elem_off[p]) return fail(FE2_EINVAL, "element offsets decrease");
     }
     const int64_t N = node_off[n_rve], E = elem_off[n_rve];
     if (E > 0 && (!conn || !EA)) return fail(FE2_EINVAL, "NULL conn or EA");
+    if (2 * E >= ((int64_t)1 << 31)) return fail(FE2_EINVAL, "too many elements in one batch");
 
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -279,15 +345,17 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     b->smem_optin = prop.sharedMemPerBlockOptin;
     b->rve.resize(n_rve);
     b->perm_to_orig.resize(N);
-    b->n_nodes_of.resize(n_rve);
-    b->is_fixed_perm.resize(N);
+    b->part_free_max.resize(n_rve);
+    const int target = std::max(64, env_int("FE2_NODES_PER_CTA", 1024));
+    const size_t smem_cap = b->smem_optin - 16384;
 
-    // ---- packing: permutation, CSR rows, element list ----
+    // ---- packing: parts, permutation, CSR rows, element list ----
     std::vector<double> hX(3 * N);
     std::vector<double> hEAcsr(2 * E), hElEA(E);
-    std::vector<int32_t> hcol(2 * E), hEla(E), hElb(E);
+    std::vector<int32_t> hcol(2 * E), hcolp(2 * E), hEla(E), hElb(E);
     std::vector<int64_t> hElemOf(2 * E), hGa(E), hGb(E);
     std::vector<int32_t> hrow((size_t)N + n_rve);
+    std::vector<int32_t> hpart((size_t)n_rve * 2 * (kMaxParts + 1), 0);
     int64_t csr_pos = 0;
     for (int32_t p = 0; p < n_rve; ++p) {
         const int64_t base = node_off[p];
@@ -297,22 +365,52 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         for (int64_t e = e0; e < e0 + ne; ++e) { deg[conn[2 * e]]++; deg[conn[2 * e + 1]]++; }
         std::vector<uint8_t> fx(n);
         for (int i = 0; i < n; ++i) fx[i] = (fixed[base + i] != 0) || deg[i] == 0;
-        // free nodes first, by degree (descending), then fixed nodes; stable by id
-        std::vector<int> order(n);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-            if (fx[x] != fx[y]) return fx[x] < fx[y];
-            if (!fx[x]) return deg[x] > deg[y];
-            return false;
-        });
-        std::vector<int> newid(n);
-        int nfree = 0, maxdeg = 0;
-        for (int k = 0; k < n; ++k) {
-            newid[order[k]] = k;
-            if (!fx[order[k]]) ++nfree;
-            maxdeg = std::max(maxdeg, deg[order[k]]);
+        const int C = choose_parts(n, target, smem_cap);
+        std::vector<int> all(n);
+        std::iota(all.begin(), all.end(), 0);
+        std::vector<std::vector<int>> parts;
+        rcb(all, C, X, base, parts);
+        // order: free nodes part by part (degree-sorted), then fixed part by part
+        std::vector<int> order;
+        order.reserve(n);
+        std::vector<int> owner(n), local(n);
+        int32_t *pf = hpart.data() + (size_t)p * 2 * (kMaxParts + 1);
+        int32_t *pg = pf + (kMaxParts + 1);
+        std::vector<std::vector<int>> fr(C), fxd(C);
+        for (int r = 0; r < C; ++r) {
+            for (int i : parts[r]) (fx[i] ? fxd[r] : fr[r]).push_back(i);
+            std::stable_sort(fr[r].begin(), fr[r].end(), [&](int x, int y) {
+                return deg[x] > deg[y] || (deg[x] == deg[y] && x < y);
+            });
+            std::sort(fxd[r].begin(), fxd[r].end());
         }
-        // CSR rows in permuted order, entries sorted by ORIGINAL neighbour id.
+        int nfree = 0, part_max = 0, free_max = 0;
+        for (int r = 0; r < C; ++r) {
+            pf[r] = nfree;
+            for (size_t k = 0; k < fr[r].size(); ++k) {
+                owner[fr[r][k]] = r;
+                local[fr[r][k]] = (int)k;
+                order.push_back(fr[r][k]);
+            }
+            nfree += (int)fr[r].size();
+            part_max = std::max(part_max, (int)(fr[r].size() + fxd[r].size()));
+            free_max = std::max(free_max, (int)fr[r].size());
+        }
+        for (int r = C; r <= kMaxParts; ++r) pf[r] = nfree;
+        int nfixed = 0;
+        for (int r = 0; r < C; ++r) {
+            pg[r] = nfixed;
+            for (size_t k = 0; k < fxd[r].size(); ++k) {
+                owner[fxd[r][k]] = r;
+                local[fxd[r][k]] = (int)(fr[r].size() + k);
+                order.push_back(fxd[r][k]);
+            }
+            nfixed += (int)fxd[r].size();
+        }
+        for (int r = C; r <= kMaxParts; ++r) pg[r] = nfixed;
+        std::vector<int> newid(n);
+        for (int k = 0; k < n; ++k) newid[order[k]] = k;
+        // CSR rows in permuted order, entries sorted by ORIGINAL neighbour id
         std::vector<std::vector<std::pair<int, int64_t>>> rows(n);
         for (int64_t e = e0; e < e0 + ne; ++e) {
             const int a = conn[2 * e], c = conn[2 * e + 1];
@@ -327,32 +425,33 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         R.n_nodes = n;
         R.n_free = nfree;
         R.n_elems = (int32_t)ne;
-        R.max_deg = maxdeg;
+        R.n_parts = C;
         R.dtc = 0.0;
         R.c = damping ? damping[p] : 0.002 * std::cbrt(512.0 / (double)n);
         R.V0 = V0 ? V0[p] : 1.0;
-        R.pad = 0.0;
-        b->n_nodes_of[p] = n;
-        int32_t local = 0;
+        R.part_max = part_max;
+        R.pad = 0;
+        b->part_free_max[p] = free_max;
+        int32_t pos = 0;
         for (int k = 0; k < n; ++k) {
             const int orig = order[k];
             b->perm_to_orig[base + k] = base + orig;
-            b->is_fixed_perm[base + k] = fx[orig];
             for (int r = 0; r < 3; ++r) hX[r * N + base + k] = X[3 * (base + orig) + r];
             auto &row = rows[orig];
             std::sort(row.begin(), row.end());
-            hrow[R.rp0 + k] = local;
+            hrow[R.rp0 + k] = pos;
             for (auto &pr : row) {
-                hcol[csr_pos + local] = newid[pr.first];
-                hElemOf[csr_pos + local] = pr.second;
-                hEAcsr[csr_pos + local] = EA[pr.second];
-                ++local;
+                hcol[csr_pos + pos] = newid[pr.first];
+                hcolp[csr_pos + pos] = (owner[pr.first] << 16) | local[pr.first];
+                hElemOf[csr_pos + pos] = pr.second;
+                hEAcsr[csr_pos + pos] = EA[pr.second];
+                ++pos;
             }
         }
-        hrow[R.rp0 + n] = local;
-        csr_pos += local;
+        hrow[R.rp0 + n] = pos;
+        csr_pos += pos;
         for (int64_t e = e0; e < e0 + ne; ++e) {
-            // keep the caller's orientation (a, b) for the stress sum
+            // the caller's orientation (a, b) is kept for lengths and the stress sum
             hEla[e] = newid[conn[2 * e]];
             hElb[e] = newid[conn[2 * e + 1]];
             hGa[e] = base + newid[conn[2 * e]];
@@ -360,9 +459,6 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
             hElEA[e] = EA[e];
         }
     }
-    // The oracle-order guarantee needs a < b in the caller's numbering for the
-    // length orientation only through squares, which are symmetric; the stress
-    // uses the caller's (a, b) as given.
 
     // ---- device allocation and upload ----
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -376,13 +472,19 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     DevBuf<int64_t> d_elemof, d_ga, d_gb;
     A(b->d_rve.alloc(n_rve), "rve");
     A(b->d_X.alloc(3 * N), "X");
+    A(b->d_Xh.alloc(3 * N), "Xh");
+    A(b->d_Xl.alloc(3 * N), "Xl");
     A(b->d_mass.alloc(N), "mass");
-    A(b->d_inv_mass_f.alloc(N), "inv_mass");
+    A(b->d_imh.alloc(N), "imh");
+    A(b->d_iml.alloc(N), "iml");
     A(b->d_EA_csr.alloc(2 * E), "EA_csr");
     A(b->d_L_csr.alloc(2 * E), "L_csr");
     A(b->d_eaf.alloc(2 * E), "eaf");
+    A(b->d_eaf_lo.alloc(2 * E), "eaf_lo");
     A(b->d_col.alloc(2 * E), "col");
+    A(b->d_col_part.alloc(2 * E), "col_part");
     A(b->d_rowptr.alloc(N + n_rve), "rowptr");
+    A(b->d_part_off.alloc(hpart.size()), "part_off");
     A(b->d_el_a.alloc(E), "el_a");
     A(b->d_el_b.alloc(E), "el_b");
     A(b->d_el_EA.alloc(E), "el_EA");
@@ -390,32 +492,37 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     A(b->d_u.alloc(3 * N), "u");
     A(b->d_v.alloc(3 * N), "v");
     A(b->d_a.alloc(3 * N), "a");
+    A(b->d_xg.alloc(3 * N), "xg");
+    A(b->d_uh.alloc(3 * N), "uh");
+    A(b->d_ul.alloc(3 * N), "ul");
+    A(b->d_vh.alloc(3 * N), "vh");
+    A(b->d_vl.alloc(3 * N), "vl");
+    A(b->d_ah.alloc(3 * N), "ah");
+    A(b->d_al.alloc(3 * N), "al");
+    A(b->d_fg.alloc(3 * N), "fg");
     A(b->d_F.alloc(9 * (size_t)n_rve), "F");
     A(b->d_sigma.alloc(9 * (size_t)n_rve), "sigma");
     A(b->d_rel.alloc(n_rve), "rel");
     A(b->d_fref.alloc(n_rve), "fref");
     A(b->d_ke.alloc(n_rve), "ke");
     A(b->d_iters.alloc(n_rve), "iters");
+    A(b->d_lead.alloc(n_rve), "lead");
     A(b->d_status.alloc(n_rve), "status");
     A(b->d_queue.alloc(2 * (size_t)n_rve), "queue");
     A(b->d_counters.alloc(32), "counters");
     A(d_elemof.alloc(2 * E), "elemof");
     A(d_ga.alloc(E), "ga");
     A(d_gb.alloc(E), "gb");
-    if (rc != FE2_OK) {
-        d_elemof.release(); d_ga.release(); d_gb.release();
-        b->release();
-        delete b;
-        return rc;
-    }
     auto H2D = [&](void *dst, const void *src, size_t bytes, const char *what) {
-        if (bytes) A(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), what);
+        if (bytes && rc == FE2_OK) A(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), what);
     };
     H2D(b->d_rve.p, b->rve.data(), sizeof(RveDesc) * n_rve, "rve");
     H2D(b->d_X.p, hX.data(), sizeof(double) * 3 * N, "X");
     H2D(b->d_EA_csr.p, hEAcsr.data(), sizeof(double) * 2 * E, "EA_csr");
     H2D(b->d_col.p, hcol.data(), sizeof(int32_t) * 2 * E, "col");
+    H2D(b->d_col_part.p, hcolp.data(), sizeof(int32_t) * 2 * E, "col_part");
     H2D(b->d_rowptr.p, hrow.data(), sizeof(int32_t) * (N + n_rve), "rowptr");
+    H2D(b->d_part_off.p, hpart.data(), sizeof(int32_t) * hpart.size(), "part_off");
     H2D(b->d_el_a.p, hEla.data(), sizeof(int32_t) * E, "el_a");
     H2D(b->d_el_b.p, hElb.data(), sizeof(int32_t) * E, "el_b");
     H2D(b->d_el_EA.p, hElEA.data(), sizeof(double) * E, "el_EA");
@@ -424,43 +531,30 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     H2D(d_gb.p, hGb.data(), sizeof(int64_t) * E, "gb");
     if (rc == FE2_OK) A(cudaMemsetAsync(b->d_u.p, 0, sizeof(double) * 3 * N, st), "u zero");
     if (rc == FE2_OK) {
-        int e = launch_setup(n_rve, E, 2 * E, b->d_rve.p, d_ga.p, d_gb.p, b->d_X.p, b->d_X.p + N,
-                             b->d_X.p + 2 * N, d_elemof.p, b->d_EA_csr.p, b->d_el_EA.p,
-                             b->d_rowptr.p, b->d_el_L.p, b->d_L_csr.p, b->d_eaf.p, b->d_mass.p,
-                             b->d_inv_mass_f.p, st);
+        const int e = launch_setup(n_rve, E, 2 * E, b->d_rve.p, d_ga.p, d_gb.p, b->d_X.p,
+                                   b->d_X.p + N, b->d_X.p + 2 * N, d_elemof.p, b->d_EA_csr.p,
+                                   b->d_el_EA.p, b->d_rowptr.p, b->d_el_L.p, b->d_L_csr.p,
+                                   b->d_eaf.p, b->d_eaf_lo.p, b->d_mass.p, b->d_imh.p,
+                                   b->d_iml.p, b->d_Xh.p, b->d_Xl.p, N, st);
         A((cudaError_t)e, "setup kernels");
     }
-    if (rc == FE2_OK) A(cudaMemcpyAsync(b->rve.data(), b->d_rve.p, sizeof(RveDesc) * n_rve,
-                                        cudaMemcpyDeviceToHost, st), "rve readback");
+    if (rc == FE2_OK)
+        A(cudaMemcpyAsync(b->rve.data(), b->d_rve.p, sizeof(RveDesc) * n_rve, cudaMemcpyDeviceToHost, st),
+          "rve readback");
     if (rc == FE2_OK) A(cudaStreamSynchronize(st), "create sync");
     d_elemof.release(); d_ga.release(); d_gb.release();
-    if (rc != FE2_OK) {
-        b->release();
-        delete b;
-        return rc;
-    }
-    build_classes(b, FE2_PREC_FP64, b->classes_fp64);
-    build_classes(b, FE2_PREC_MIXED, b->classes_mixed);
-    {
+    if (rc == FE2_OK) {
+        build_classes(b, FE2_PREC_FP64, b->classes_fp64);
+        build_classes(b, FE2_PREC_MIXED, b->classes_mixed);
         // work queues: per class, RVE ids in scheduling order (FP64, then mixed)
         std::vector<int32_t> q(2 * (size_t)n_rve);
         for (auto &c : b->classes_fp64) std::copy(c.rves.begin(), c.rves.end(), q.begin() + c.queue_off);
         for (auto &c : b->classes_mixed)
             std::copy(c.rves.begin(), c.rves.end(), q.begin() + n_rve + c.queue_off);
-        A(cudaMemcpy(b->d_queue.p, q.data(), sizeof(int32_t) * 2 * n_rve, cudaMemcpyHostToDevice),
-          "queue");
+        A(cudaMemcpy(b->d_queue.p, q.data(), sizeof(int32_t) * 2 * n_rve, cudaMemcpyHostToDevice), "queue");
         A(cudaMallocHost(&b->h_F, sizeof(double) * 9 * n_rve), "pinned F");
         A(cudaEventCreateWithFlags(&b->ev_F, cudaEventDisableTiming), "F event");
     }
-    // scratch for RVEs that stage positions in L2 instead of shared memory
-    bool need_xg = false, need_pg = false;
-    for (auto &c : b->classes_fp64) need_xg |= !c.smem_positions;
-    for (auto &c : b->classes_mixed) need_pg |= !c.smem_positions;
-    if (need_xg) A(b->d_xg.alloc(3 * N), "xg");
-    if (need_pg) A(b->d_pg.alloc(2 * N), "pg");
-    A(b->d_fv.alloc(3 * N), "fv");
-    A(b->d_fa.alloc(3 * N), "fa");
-    A(b->d_fg.alloc(3 * N), "fg");
     for (int k = 0; k < 6 && rc == FE2_OK; ++k) {
         cudaStream_t s;
         A(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
@@ -496,14 +590,20 @@ fe2_status check_opts(const fe2_opts &o) {
     if (o.init < 0 || o.init > 2) return fail(FE2_EINVAL, "unknown init");
     if (o.block_threads != 0 && (o.block_threads < 64 || o.block_threads > 512 || o.block_threads % 32))
         return fail(FE2_EINVAL, "block_threads must be 0 or a multiple of 32 in [64, 512]");
+    if (!(o.lead_tol >= 0.0) || !std::isfinite(o.lead_tol)) return fail(FE2_EINVAL, "lead_tol must be finite and >= 0");
     return FE2_OK;
+}
+
+int mixed_block(const SizeClass &c, int requested) {
+    if (requested) return requested;
+    int t = ((c.free_max + 31) / 32) * 32;
+    return std::max(128, std::min(512, t));
 }
 
 fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
     const bool fp64 = o.precision == FE2_PREC_FP64;
     auto &classes = fp64 ? b->classes_fp64 : b->classes_mixed;
     CUDA_TRY(cudaMemsetAsync(b->d_counters.p, 0, sizeof(int32_t) * 32, st));
-    const int block = o.block_threads ? o.block_threads : 512;
     SolveParams P;
     P.F = b->d_F.p;
     P.tol = o.tol;
@@ -512,6 +612,7 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
     P.init = o.init;
     P.want_ke = o.kinetic_energy;
     P.lead_iters = o.lead_iters;
+    P.lead_tol = o.lead_tol;
     P.rebase_every = o.rebase_every;
     const DevMesh M = b->mesh();
     const DevState S = b->state();
@@ -527,16 +628,25 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
         P.queue_len = (int32_t)c.rves.size();
         P.counter = b->d_counters.p + k;
         P.smem_positions = c.smem_positions;
-        const size_t smem = c.smem_positions ? c.smem_bytes : 0;
-        int per_sm = fp64 ? occupancy_dr_fp64(c.smem_positions, block, smem)
-                          : occupancy_dr_mixed(c.smem_positions, block, smem);
-        per_sm = std::max(1, per_sm);
-        const int grid = std::max(1, std::min<int>((int)c.rves.size(), per_sm * b->sm_count));
         CUDA_TRY(cudaEventRecord(b->tev[2 * k], s));
-        const int e = fp64 ? launch_dr_fp64(M, S, R, P, grid, block, smem, s)
-                           : launch_dr_mixed(M, S, R, P, grid, block, smem, s);
-        CUDA_TRY(cudaEventRecord(b->tev[2 * k + 1], s));
+        int e;
+        if (fp64) {
+            const int block = o.block_threads ? o.block_threads : 512;
+            const size_t smem = c.smem_positions ? c.smem_bytes : 0;
+            const int per_sm = std::max(1, occupancy_dr_fp64(c.smem_positions, block, smem));
+            const int grid = std::max(1, std::min<int>((int)c.rves.size(), per_sm * b->sm_count));
+            e = launch_dr_fp64(M, S, R, P, grid, block, smem, s);
+        } else {
+            const int block = mixed_block(c, o.block_threads);
+            const int resident = occupancy_dr_mixed(c.parts, block, c.smem_bytes);
+            if (resident < 1)
+                return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
+                                           std::to_string(c.smem_bytes) + " B shared memory fits");
+            const int clusters = std::max(1, std::min<int>((int)c.rves.size(), resident));
+            e = launch_dr_mixed(M, S, R, P, clusters, c.parts, block, c.smem_bytes, s);
+        }
         if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
+        CUDA_TRY(cudaEventRecord(b->tev[2 * k + 1], s));
         ++launches;
         CUDA_TRY(cudaEventRecord(b->ev[1 + k], s));
         CUDA_TRY(cudaStreamWaitEvent(st, b->ev[1 + k], 0));
@@ -590,6 +700,18 @@ extern "C" fe2_status fe2_batch_stress(fe2_batch *b, double *sigma, int64_t *ite
     if (iters) CUDA_TRY(cudaMemcpy(iters, b->d_iters.p, sizeof(int64_t) * P, cudaMemcpyDeviceToHost));
     if (rel_res) CUDA_TRY(cudaMemcpy(rel_res, b->d_rel.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
     if (status) CUDA_TRY(cudaMemcpy(status, b->d_status.p, sizeof(int32_t) * P, cudaMemcpyDeviceToHost));
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_diagnostics(fe2_batch *b, double *f_ref, double *kinetic_energy,
+                                            int64_t *lead_iters) {
+    if (!b) return fail(FE2_EINVAL, "NULL batch");
+    if (!b->solved) return fail(FE2_ESTATE, "no solve has been issued");
+    CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    const size_t P = b->n_rve;
+    if (f_ref) CUDA_TRY(cudaMemcpy(f_ref, b->d_fref.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    if (kinetic_energy) CUDA_TRY(cudaMemcpy(kinetic_energy, b->d_ke.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    if (lead_iters) CUDA_TRY(cudaMemcpy(lead_iters, b->d_lead.p, sizeof(int64_t) * P, cudaMemcpyDeviceToHost));
     return FE2_OK;
 }
 
@@ -652,6 +774,12 @@ extern "C" fe2_status fe2_batch_kernel_times(fe2_batch *b, float *ms, int32_t ca
         CUDA_TRY(cudaEventSynchronize(b->tev[2 * k + 1]));
         CUDA_TRY(cudaEventElapsedTime(ms + k, b->tev[2 * k], b->tev[2 * k + 1]));
     }
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_parts(const fe2_batch *b, int32_t *parts) {
+    if (!b || !parts) return fail(FE2_EINVAL, "NULL batch or parts");
+    for (int32_t p = 0; p < b->n_rve; ++p) parts[p] = b->rve[p].n_parts;
     return FE2_OK;
 }
 
