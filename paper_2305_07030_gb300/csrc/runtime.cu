@@ -594,10 +594,12 @@ fe2_status check_opts(const fe2_opts &o) {
     return FE2_OK;
 }
 
+// Threads per CTA of the mixed solver. A fixed default keeps every RVE's
+// result independent of which other RVEs share its launch (the residual's
+// partial sums follow the thread-to-node mapping).
 int mixed_block(const SizeClass &c, int requested) {
-    if (requested) return requested;
-    int t = ((c.free_max + 31) / 32) * 32;
-    return std::max(128, std::min(512, t));
+    (void)c;
+    return requested ? requested : 256;
 }
 
 fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
