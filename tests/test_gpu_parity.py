@@ -87,7 +87,7 @@ def test_mixed_within_tolerance_or_rounding_envelope():
         assert out["status"][p] == "OK"
         assert res <= 1.5e-8, (p, res)
         assert rel_err(out["sigma"][p], s_at_u) <= 1e-12
-        assert e <= max(1e-5, 2.0 * spread), rows
+        assert e <= (1e-5 if spread <= 1e-6 else 10.0 * spread), rows
     print("mixed (p, n, err, oracle envelope, oracle residual at GPU state):", rows)
     # the well-conditioned RVEs keep the oracle's equilibrium closely
     assert sum(1 for row in rows if row[3] <= 1e-6) >= 2
