@@ -1,21 +1,24 @@
 // Mixed-precision dynamic relaxation (Algorithm 1) for a batch of RVEs: one
-// thread-block cluster per RVE, whole loop inside one persistent launch.
+// thread-block cluster per RVE, two persistent launches per size class.
 //
 // Layout. The RVE is split spatially into `parts` pieces, one per CTA of the
-// cluster; a CTA stages the current positions of its own nodes in its shared
-// memory and reads neighbours owned by other CTAs through distributed shared
-// memory. The paper used one thread team per sub-problem (Section III); a
-// cluster lets one sub-problem span several SMs when one team is not enough.
+// cluster; a CTA stages the state of its own nodes in its shared memory and
+// reads neighbours owned by other CTAs through distributed shared memory. The
+// paper used one thread team per sub-problem (Section III); a cluster lets one
+// sub-problem span several SMs.
 //
-// Precision. All arithmetic runs on the FP32 pipes (GB300's FP64 rate is a
-// small fraction of FP32):
-//  * lead phase: double-float (hi + lo FP32 pairs, ~48 bits) positions,
-//    velocities, accelerations and element forces until the relative residual
+// Precision. All arithmetic of the iterations runs on the FP32 pipes (GB300
+// issues FP64 at roughly 1/70 of the FP32 rate):
+//  * lead kernel: double-float (hi + lo FP32 pairs, ~48 bits) displacement,
+//    velocity, acceleration and element forces until the relative residual
 //    first drops below lead_tol. Random fiber networks are not isostatic and
 //    can pass bifurcation points (Section II); which equilibrium the
 //    relaxation settles into is decided in this transient and is sensitive to
-//    force errors far below FP32 rounding;
-//  * FP32 phase: each element force is an exact increment about a reference
+//    force errors far below FP32 rounding. Element forces are evaluated in
+//    displacement form, d = D + (u_j - u_i) with D = X_j - X_i, and
+//    N/l = EA h / (L l (l + L)), h = l^2 - L^2 = (u_j - u_i).(D + d), which
+//    has no cancellation, so the double-float strain is accurate to ~1e-14;
+//  * FP32 kernel: each element force is an exact increment about a reference
 //    state x_ref,
 //        t(d_ref + dd) = t(d_ref) + q_ref dd + dq (d_ref + dd),
 //        q = N/l = EA (1/L - 1/l),  dq = EA h / (l l_ref (l + l_ref)),
@@ -25,15 +28,14 @@
 //    iterations, when the FP32 increment du is folded into the double-float
 //    displacement. Velocity and increment updates are FP32;
 //  * the residual norm is summed per warp in FP32 (squares, no cancellation)
-//    and across warps and CTAs in double-float; the convergence threshold
-//    (tol f_ref)^2 is formed in FP64 and compared in double-float; the
-//    stress sum is FP64. FP64 instructions stay out of the iteration loop:
-//    GB300 issues them at roughly 1/70 of the FP32 rate.
+//    and across warps and CTAs in double-float; the threshold (tol f_ref)^2 is
+//    formed in FP64 once per RVE; the stress sum is FP64.
 //
-// Synchronisation. The FP32 phase keeps two increment buffers (ping-pong), so
-// one cluster barrier per iteration suffices: iteration n writes buffer n&1,
-// the barrier publishes it, and the residual of iteration n-1 is tested right
-// after that barrier (its state, buffer (n-1)&1, is still intact).
+// Synchronisation of the FP32 kernel. Three increment buffers rotate, so one
+// cluster barrier per iteration suffices and the residual reduction of
+// iteration n-2 runs between the barrier's arrive and wait of iteration n,
+// hidden behind the barrier latency; its state (buffer (n-2) mod 3) is still
+// intact when the test succeeds.
 #include <cooperative_groups.h>
 
 #include "df64.cuh"
@@ -46,17 +48,18 @@ namespace fe2 {
 namespace {
 
 constexpr int kMaxWarps = 16;  // blocks of at most 512 threads
+constexpr int kBufs = 3;       // rotating increment / partial buffers
 
 struct MixedShared {
-    float red[2][kMaxParts][kMaxWarps];   // per-warp residual partials of every CTA
-    float kred[2][kMaxParts][kMaxWarps];  // kinetic-energy partials
-    double sig[kMaxParts][9];             // stress partials, read by rank 0
-    double wsum[kMaxWarps][9];            // per-warp stress partials
-    float4 *P[kMaxParts];                 // every CTA's x_ref / position-hi array
-    float4 *Q[2][kMaxParts];              // every CTA's increment / position-lo arrays
-    float *redp[kMaxParts];               // every CTA's red
-    float *kredp[kMaxParts];              // every CTA's kred
-    double *sigp;                         // rank 0's sig
+    float red[kBufs][kMaxParts][kMaxWarps];   // per-warp residual partials of every CTA
+    float kred[kBufs][kMaxParts][kMaxWarps];  // kinetic-energy partials
+    double sig[kMaxParts][9];                 // stress partials, read by rank 0
+    double wsum[kMaxWarps][9];                // per-warp stress partials
+    float4 *P[kMaxParts];                     // every CTA's position array
+    float4 *Q[kBufs][kMaxParts];              // every CTA's increment / low-part arrays
+    float *redp[kMaxParts];                   // every CTA's red
+    float *kredp[kMaxParts];                  // every CTA's kred
+    double *sigp;                             // rank 0's sig
     int item;
 };
 
@@ -68,6 +71,26 @@ struct Part {
     __device__ int gidx(int k) const { return k < nfr ? f0 + k : nf + g0 + (k - nfr); }
     __device__ int m() const { return nfr + nfx; }
 };
+
+__device__ __forceinline__ Part make_part(const DevMesh &M, const RveDesc &R, int p, int me, int C) {
+    const int32_t *po = M.part_off + (int64_t)p * 2 * (kMaxParts + 1);
+    Part pt;
+    pt.me = me;
+    pt.C = C;
+    pt.nf = R.n_free;
+    pt.f0 = po[me];
+    pt.nfr = po[me + 1] - pt.f0;
+    pt.g0 = po[kMaxParts + 1 + me];
+    pt.nfx = po[kMaxParts + 1 + me + 1] - pt.g0;
+    return pt;
+}
+
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
 
 // Double-float total of the cluster's per-warp partials (buffer `buf`),
 // computed warp-parallel on the FP32 pipes: lane l adds entries l, l+32, ...
@@ -104,15 +127,16 @@ __device__ __forceinline__ void publish(MixedShared &sh, const Part &pt, float v
     }
 }
 
-// Double-float internal force on own node k (Algorithm 1, getInternalForces),
-// gathered over its CSR row: g = sum_j EA (1/L - 1/l) (x_j - x_i).
+// Double-float internal force on own node k (Algorithm 1, getInternalForces)
+// in displacement form; the node's and its neighbours' displacements are
+// staged as (hi, lo) in (Pl, Ql) and the other CTAs' copies (Q buffer qbuf).
 __device__ __forceinline__ void gather_df(const DevMesh &M, const RveDesc &R, const int32_t *rowptr,
                                           const MixedShared &sh, const Part &pt, int k,
                                           const float4 *Pl, const float4 *Ql, int qbuf, df &g0,
                                           df &g1, df &g2) {
     const int gi = pt.gidx(k);
     const float4 pi = Pl[k], qi = Ql[k];
-    const df xi0 = {pi.x, qi.x}, xi1 = {pi.y, qi.y}, xi2 = {pi.z, qi.z};
+    const df ui0 = {pi.x, qi.x}, ui1 = {pi.y, qi.y}, ui2 = {pi.z, qi.z};
     g0 = df_from(0.f); g1 = df_from(0.f); g2 = df_from(0.f);
     const int beg = rowptr[gi], end = rowptr[gi + 1];
     for (int e = beg; e < end; ++e) {
@@ -121,62 +145,80 @@ __device__ __forceinline__ void gather_df(const DevMesh &M, const RveDesc &R, co
         const int r = cp >> 16, loc = cp & 0xffff;
         const float4 pj = r == pt.me ? Pl[loc] : sh.P[r][loc];
         const float4 qj = r == pt.me ? Ql[loc] : sh.Q[qbuf][r][loc];
-        const df d0 = df_sub({pj.x, qj.x}, xi0);
-        const df d1 = df_sub({pj.y, qj.y}, xi1);
-        const df d2 = df_sub({pj.z, qj.z}, xi2);
-        const df l2 = df_add(df_add(df_sqr(d0), df_sqr(d1)), df_sqr(d2));
+        const float4 Dh = M.dh[kk], Dl = M.dl[kk];
+        // relative displacement and current element vector
+        const df e0 = df_sub({pj.x, qj.x}, ui0), e1 = df_sub({pj.y, qj.y}, ui1),
+                 e2 = df_sub({pj.z, qj.z}, ui2);
+        const df D0 = {Dh.x, Dl.x}, D1 = {Dh.y, Dl.y}, D2 = {Dh.z, Dl.z}, L = {Dh.w, Dl.w};
+        const df d0 = df_add(D0, e0), d1 = df_add(D1, e1), d2 = df_add(D2, e2);
+        // h = l^2 - L^2 = e.(D + d)
+        const df h = df_add(df_add(df_mul(e0, df_add(D0, d0)), df_mul(e1, df_add(D1, d1))),
+                            df_mul(e2, df_add(D2, d2)));
+        const df l2 = df_add(df_sqr(L), h);
         const df rl = df_rsqrt(l2);
+        const df l = df_mul(l2, rl);
         const float2 eh = M.eaf[kk], el = M.eaf_lo[kk];
-        const df q = df_mul({eh.x, el.x}, df_sub({eh.y, el.y}, rl));
+        // N/l = EA (l - L) / (L l) = (EA/L) h / (l (l + L))
+        const df kax = df_mul({eh.x, el.x}, {eh.y, el.y});
+        const df q = df_mul(df_mul(kax, df_mul(h, rl)), df_rcp(df_add(l, L)));
         g0 = df_add(g0, df_mul(q, d0));
         g1 = df_add(g1, df_mul(q, d1));
         g2 = df_add(g2, df_mul(q, d2));
     }
 }
 
-__device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M,
-                                const DevState &S, const DevResults &O, const SolveParams &P,
-                                int p, float4 *Pl, float4 *Q0, float4 *Q1, int &rb) {
+__device__ __forceinline__ void map_remote(cg::cluster_group &cl, MixedShared &sh, float4 *Pl,
+                                           float4 *const *Qb, int C) {
+    if ((int)threadIdx.x < C) {
+        const int r = threadIdx.x;
+        sh.P[r] = cl.map_shared_rank(Pl, r);
+        for (int b = 0; b < kBufs; ++b) sh.Q[b][r] = cl.map_shared_rank(Qb[b], r);
+        sh.redp[r] = cl.map_shared_rank(&sh.red[0][0][0], r);
+        sh.kredp[r] = cl.map_shared_rank(&sh.kred[0][0][0], r);
+    }
+    if (threadIdx.x == 0) sh.sigp = cl.map_shared_rank(&sh.sig[0][0], 0);
+}
+
+// Next work item of the cluster (rank 0 pops, everyone reads it).
+__device__ __forceinline__ int next_item(cg::cluster_group &cl, MixedShared &sh, int32_t *counter) {
+    if (cl.block_rank() == 0 && threadIdx.x == 0) sh.item = atomicAdd(counter, 1);
+    cl.sync();
+    const int item = *cl.map_shared_rank(&sh.item, 0);
+    cl.sync();
+    return item;
+}
+
+// ---------------------------------------------------------------------------
+// lead kernel: setup (Algorithm 1 lines up to the loop) and the double-float
+// iterations
+// ---------------------------------------------------------------------------
+__device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
+                         const DevResults &O, const SolveParams &P, int p, float4 *Pl, float4 *Q0,
+                         int &rb) {
     const RveDesc R = M.rve[p];
-    const int n = R.n_nodes, nf = R.n_free;
+    const Part pt = make_part(M, R, p, (int)cl.block_rank(), (int)cl.num_blocks());
+    const int n = R.n_nodes, m = pt.m();
     const int64_t n0 = R.node0, b3 = 3 * n0;
     const int32_t *rowptr = M.rowptr + R.rp0;
-    const int32_t *po = M.part_off + (int64_t)p * 2 * (kMaxParts + 1);
-    Part pt;
-    pt.me = (int)cl.block_rank();
-    pt.C = (int)cl.num_blocks();
-    pt.nf = nf;
-    pt.f0 = po[pt.me];
-    pt.nfr = po[pt.me + 1] - pt.f0;
-    pt.g0 = po[kMaxParts + 1 + pt.me];
-    pt.nfx = po[kMaxParts + 1 + pt.me + 1] - pt.g0;
-    const int m = pt.m();
     double F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = P.F[9 * (int64_t)p + k];
-    // per-RVE [3][n] blocks
-    const float *Xh = M.Xh + b3, *Xl = M.Xl + b3;
     float *uh = S.uh + b3, *ul = S.ul + b3, *vh = S.vh + b3, *vl = S.vl + b3;
     float *ah = S.ah + b3, *al = S.al + b3, *fg = S.fg + b3;
     const float *imh = M.imh + n0, *iml = M.iml + n0;
-    double *xg = S.xg + b3;
     const bool want_k = P.want_ke != 0;
-    float4 *Qb[2] = {Q0, Q1};
 
-    // ---- setup: affine positions, f_ref, initial state (Algorithm 1) ----
+    // affine displacement (F - I) X for f_ref, and the initial displacement
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int i = pt.gidx(k);
         const double X[3] = {M.X0[n0 + i], M.X1[n0 + i], M.X2[n0 + i]};
-        double xa[3];
-        for (int r = 0; r < 3; ++r)
-            xa[r] = dadd(dadd(dmul(F[3 * r], X[0]), dmul(F[3 * r + 1], X[1])), dmul(F[3 * r + 2], X[2]));
-        const df a0 = df_from_double(xa[0]), a1 = df_from_double(xa[1]), a2 = df_from_double(xa[2]);
-        Pl[k] = make_float4(a0.hi, a1.hi, a2.hi, 0.f);
-        Q0[k] = make_float4(a0.lo, a1.lo, a2.lo, 0.f);
-        const bool fixed = k >= pt.nfr;
         const double *uw[3] = {S.u0 + n0, S.u1 + n0, S.u2 + n0};
+        df ua[3];
+        const bool fixed = k >= pt.nfr;
         for (int r = 0; r < 3; ++r) {
-            const double uaff = dsub(xa[r], X[r]);
+            const double xa = dadd(dadd(dmul(F[3 * r], X[0]), dmul(F[3 * r + 1], X[1])), dmul(F[3 * r + 2], X[2]));
+            const double uaff = dsub(xa, X[r]);
+            ua[r] = df_from_double(uaff);
             double u;
             if (fixed || P.init == 1) u = uaff;
             else if (P.init == 2) u = uw[r][i];
@@ -185,6 +227,8 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
             uh[r * n + i] = ud.hi;
             ul[r * n + i] = ud.lo;
         }
+        Pl[k] = make_float4(ua[0].hi, ua[1].hi, ua[2].hi, 0.f);
+        Q0[k] = make_float4(ua[0].lo, ua[1].lo, ua[2].lo, 0.f);
     }
     cl.sync();
     float acc = 0.f;
@@ -196,14 +240,11 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
     publish(sh, pt, acc, 0.f, false, rb);
     cl.sync();
     const double f_aff = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
-    rb ^= 1;
+    rb = (rb + 1) % kBufs;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int i = pt.gidx(k);
-        df x[3];
-        for (int r = 0; r < 3; ++r)
-            x[r] = df_add({Xh[r * n + i], Xl[r * n + i]}, {uh[r * n + i], ul[r * n + i]});
-        Pl[k] = make_float4(x[0].hi, x[1].hi, x[2].hi, 0.f);
-        Q0[k] = make_float4(x[0].lo, x[1].lo, x[2].lo, 0.f);
+        Pl[k] = make_float4(uh[i], uh[n + i], uh[2 * n + i], 0.f);
+        Q0[k] = make_float4(ul[i], ul[n + i], ul[2 * n + i], 0.f);
     }
     cl.sync();
     acc = 0.f;
@@ -225,41 +266,31 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
     publish(sh, pt, acc, 0.f, false, rb);
     cl.sync();
     const double f0 = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
-    rb ^= 1;
+    rb = (rb + 1) % kBufs;
     const double f_ref = f_aff > f0 ? f_aff : f0;
-    // convergence and lead tests compare squared norms in double-float
     const df thresh2 = df_from_double(dmul(dmul(P.tol, f_ref), dmul(P.tol, f_ref)));
     const df lead2 = df_from_double(dmul(dmul(P.lead_tol, f_ref), dmul(P.lead_tol, f_ref)));
-
     const double dt64 = dmul(P.alpha, R.dtc);
     const df dt = df_from_double(dt64), hdt = df_from_double(dmul(0.5, dt64));
     const df cdf = df_from_double(R.c);
-    const float dtf = dt.hi, hdtf = hdt.hi, cf = cdf.hi;
-    const int K = P.rebase_every > 0 ? P.rebase_every : 512;
 
-    int64_t it = 0, lead = 0;
-    int status = RVE_MAXITER;
+    int64_t it = 0;
+    int status = RVE_PENDING;
     df r2 = df_from(0.f), k2 = df_from(0.f);
-    bool done = false;
-    int fin = -1;  // increment buffer holding the final state (FP32 phase), -1: none
-
-    // ---- lead phase: double-float ----
     for (;;) {
         for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
             const int i = pt.f0 + k;
-            df x[3];
+            df u[3];
             for (int c = 0; c < 3; ++c) {
                 df v = {vh[c * n + i], vl[c * n + i]};
                 const df a = {ah[c * n + i], al[c * n + i]};
                 v = df_add(v, df_mul(hdt, a));
-                df u = {uh[c * n + i], ul[c * n + i]};
-                u = df_add(u, df_mul(dt, v));
+                u[c] = df_add({uh[c * n + i], ul[c * n + i]}, df_mul(dt, v));
                 vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
-                uh[c * n + i] = u.hi; ul[c * n + i] = u.lo;
-                x[c] = df_add({Xh[c * n + i], Xl[c * n + i]}, u);
+                uh[c * n + i] = u[c].hi; ul[c * n + i] = u[c].lo;
             }
-            Pl[k] = make_float4(x[0].hi, x[1].hi, x[2].hi, 0.f);
-            Q0[k] = make_float4(x[0].lo, x[1].lo, x[2].lo, 0.f);
+            Pl[k] = make_float4(u[0].hi, u[1].hi, u[2].hi, 0.f);
+            Q0[k] = make_float4(u[0].lo, u[1].lo, u[2].lo, 0.f);
         }
         cl.sync();
         float rs = 0.f, kes = 0.f;
@@ -285,29 +316,76 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
         cl.sync();
         r2 = cluster_total(sh.red, rb, pt.C);
         if (want_k) k2 = cluster_total(sh.kred, rb, pt.C);
-        rb ^= 1;
+        rb = (rb + 1) % kBufs;
         ++it;
-        if (!isfinite(r2.hi)) { status = RVE_NAN; done = true; break; }
-        if (df_le(r2, thresh2)) { status = RVE_OK; done = true; break; }
-        if (it >= P.max_iter) { status = RVE_MAXITER; done = true; break; }
+        if (!isfinite(r2.hi)) { status = RVE_NAN; break; }
+        if (df_le(r2, thresh2)) { status = RVE_OK; break; }
+        if (it >= P.max_iter) { status = RVE_MAXITER; break; }
         if (P.lead_iters >= 0 ? it >= P.lead_iters : df_le(r2, lead2)) break;
     }
-    lead = it;
+    if (pt.me == 0 && threadIdx.x == 0) {
+        O.iters[p] = it;
+        O.lead[p] = it;
+        O.status[p] = status;
+        O.f_ref[p] = f_ref;
+        O.rel_res[p] = df_to_double(r2);  // squared residual, finished by the FP32 kernel
+        O.ke[p] = want_k ? df_to_double(k2) : 0.0;
+    }
+    cl.sync();
+}
 
-    // ---- FP32 phase: increments about a double-float reference ----
-    if (!done) {
-        // x_ref = current positions (Pl holds their FP32 rounding), g_ref = fg,
-        // increments zero. Remote reads of Q0 ended at the last barrier.
+// ---------------------------------------------------------------------------
+// FP32 kernel: increment iterations, reference refreshes, final state, stress
+// ---------------------------------------------------------------------------
+__device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
+                         const DevResults &O, const SolveParams &P, int p, float4 *Pl,
+                         float4 *const *Qb, int &rb) {
+    const RveDesc R = M.rve[p];
+    const Part pt = make_part(M, R, p, (int)cl.block_rank(), (int)cl.num_blocks());
+    const int n = R.n_nodes, m = pt.m();
+    const int64_t n0 = R.node0, b3 = 3 * n0;
+    const int32_t *rowptr = M.rowptr + R.rp0;
+    const float *Xh = M.Xh + b3, *Xl = M.Xl + b3;
+    float *uh = S.uh + b3, *ul = S.ul + b3, *vh = S.vh + b3, *ah = S.ah + b3, *fg = S.fg + b3;
+    const float *imh = M.imh + n0;
+    double *xg = S.xg + b3;
+    const bool want_k = P.want_ke != 0;
+    double F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = P.F[9 * (int64_t)p + k];
+
+    int status = O.status[p];
+    int64_t it = O.iters[p];
+    const double f_ref = O.f_ref[p];
+    df r2 = df_from_double(O.rel_res[p]);
+    df k2 = df_from_double(O.ke[p]);
+    int fin = -1;  // increment buffer holding the final state, -1: none
+    cl.sync();     // every CTA has read the lead's results before rank 0 rewrites them
+
+    if (status == RVE_PENDING) {
+        const df thresh2 = df_from_double(dmul(dmul(P.tol, f_ref), dmul(P.tol, f_ref)));
+        const double dt64 = dmul(P.alpha, R.dtc);
+        const float dtf = (float)dt64, hdtf = (float)dmul(0.5, dt64), cf = (float)R.c;
+        const int K = P.rebase_every > 0 ? P.rebase_every : 512;
+        // x_ref = X + u (FP32 rounding of the double-float sum), increments zero;
+        // g_ref = fg from the lead's last force evaluation at exactly this state
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
-            Q0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            Q1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int i = pt.gidx(k);
+            float xr[3];
+            for (int c = 0; c < 3; ++c)
+                xr[c] = df_add({Xh[c * n + i], Xl[c * n + i]}, {uh[c * n + i], ul[c * n + i]}).hi;
+            Pl[k] = make_float4(xr[0], xr[1], xr[2], 0.f);
+            for (int b = 0; b < kBufs; ++b) Qb[b][k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        int b = 0, since = 0, rbp = 0;
-        bool pending = false;
-        for (;;) {
+        cl.sync();
+        const int64_t first = it;  // evaluation index of the first FP32 iteration
+        int64_t chk = first;       // next evaluation whose residual is still untested
+        int since = 0;
+        for (int64_t nidx = first;; ++nidx) {
+            const int b = (int)(nidx % kBufs), bp = (int)((nidx + kBufs - 1) % kBufs);
             // partial velocity update; displacement increment into buffer b
             {
-                const float4 *prev = Qb[b ^ 1];
+                const float4 *prev = Qb[bp];
                 float4 *cur = Qb[b];
                 for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
                     const int i = pt.f0 + k;
@@ -315,39 +393,56 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
                     const float w1 = vh[n + i] + hdtf * ah[n + i];
                     const float w2 = vh[2 * n + i] + hdtf * ah[2 * n + i];
                     vh[i] = w0; vh[n + i] = w1; vh[2 * n + i] = w2;
-                    const float4 d = prev[k];
+                    const float4 d = nidx == first ? make_float4(0.f, 0.f, 0.f, 0.f) : prev[k];
                     cur[k] = make_float4(d.x + dtf * w0, d.y + dtf * w1, d.z + dtf * w2, 0.f);
                 }
             }
-            cl.sync();
-            if (pending) {
-                // residual of the previous iteration (its state is buffer b^1)
-                r2 = cluster_total(sh.red, rbp, pt.C);
-                if (want_k) k2 = cluster_total(sh.kred, rbp, pt.C);
-                if (!isfinite(r2.hi)) { status = RVE_NAN; fin = b ^ 1; break; }
-                if (df_le(r2, thresh2)) { status = RVE_OK; fin = b ^ 1; break; }
-                if (it >= P.max_iter) { status = RVE_MAXITER; fin = b ^ 1; break; }
+            cluster_arrive();
+            // residual test of evaluation nidx-2 while the barrier completes
+            bool stop = false;
+            if (chk <= nidx - 2) {
+                r2 = cluster_total(sh.red, (int)(chk % kBufs), pt.C);
+                if (want_k) k2 = cluster_total(sh.kred, (int)(chk % kBufs), pt.C);
+                const int64_t done = chk + 1;
+                if (!isfinite(r2.hi)) { status = RVE_NAN; stop = true; }
+                else if (df_le(r2, thresh2)) { status = RVE_OK; stop = true; }
+                else if (done >= P.max_iter) { status = RVE_MAXITER; stop = true; }
+                if (stop) { fin = (int)(chk % kBufs); it = done; }
+                ++chk;
             }
+            cluster_wait();
+            if (stop) break;
             float4 *cur = Qb[b];
             float rs = 0.f, kes = 0.f;
             if (since >= K) {
-                // Rebase: fold the increment into the double-float displacement and
-                // stage double-float positions (hi in Pl, lo in buffer b).
+                // the reference moves: every earlier evaluation must be tested first
+                if (chk == nidx - 1) {
+                    r2 = cluster_total(sh.red, (int)(chk % kBufs), pt.C);
+                    if (want_k) k2 = cluster_total(sh.kred, (int)(chk % kBufs), pt.C);
+                    const int64_t done = chk + 1;
+                    if (!isfinite(r2.hi)) { status = RVE_NAN; stop = true; }
+                    else if (df_le(r2, thresh2)) { status = RVE_OK; stop = true; }
+                    else if (done >= P.max_iter) { status = RVE_MAXITER; stop = true; }
+                    if (stop) { fin = (int)(chk % kBufs); it = done; }
+                    ++chk;
+                }
+                if (stop) break;
+                // fold the increment into the double-float displacement; stage
+                // double-float displacements (hi in Pl, lo in buffer b)
                 for (int k = threadIdx.x; k < m; k += blockDim.x) {
                     const int i = pt.gidx(k);
                     const float4 d = cur[k];
                     const float dd[3] = {d.x, d.y, d.z};
-                    df x[3];
+                    df u[3];
                     for (int c = 0; c < 3; ++c) {
-                        df u = {uh[c * n + i], ul[c * n + i]};
+                        u[c] = {uh[c * n + i], ul[c * n + i]};
                         if (k < pt.nfr) {
-                            u = df_add_f(u, dd[c]);
-                            uh[c * n + i] = u.hi; ul[c * n + i] = u.lo;
+                            u[c] = df_add_f(u[c], dd[c]);
+                            uh[c * n + i] = u[c].hi; ul[c * n + i] = u[c].lo;
                         }
-                        x[c] = df_add({Xh[c * n + i], Xl[c * n + i]}, u);
                     }
-                    Pl[k] = make_float4(x[0].hi, x[1].hi, x[2].hi, 0.f);
-                    cur[k] = make_float4(x[0].lo, x[1].lo, x[2].lo, 0.f);
+                    Pl[k] = make_float4(u[0].hi, u[1].hi, u[2].hi, 0.f);
+                    cur[k] = make_float4(u[0].lo, u[1].lo, u[2].lo, 0.f);
                 }
                 cl.sync();
                 for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
@@ -357,8 +452,16 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
                     fg[i] = g[0].hi; fg[n + i] = g[1].hi; fg[2 * n + i] = g[2].hi;
                 }
                 cl.sync();
-                for (int k = threadIdx.x; k < m; k += blockDim.x) cur[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                // accelerations and velocities from the reference force
+                // back to FP32 reference positions and zero increments
+                for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                    const int i = pt.gidx(k);
+                    float xr[3];
+                    for (int c = 0; c < 3; ++c)
+                        xr[c] = df_add({Xh[c * n + i], Xl[c * n + i]}, {uh[c * n + i], ul[c * n + i]}).hi;
+                    Pl[k] = make_float4(xr[0], xr[1], xr[2], 0.f);
+                    cur[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                cl.sync();
                 for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
                     const int i = pt.f0 + k;
                     const float im = imh[i];
@@ -389,19 +492,19 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
                         const float2 ei = M.eaf[kk];
                         const float4 pj = rr == pt.me ? Pl[loc] : sh.P[rr][loc];
                         const float4 qj = rr == pt.me ? cur[loc] : sh.Q[b][rr][loc];
-                        const float r0 = pj.x - pi.x, r1 = pj.y - pi.y, r2 = pj.z - pi.z;
+                        const float r0 = pj.x - pi.x, r1 = pj.y - pi.y, r2_ = pj.z - pi.z;
                         const float e0 = qj.x - qi.x, e1 = qj.y - qi.y, e2 = qj.z - qi.z;
-                        const float lr2 = r0 * r0 + r1 * r1 + r2 * r2;
+                        const float lr2 = r0 * r0 + r1 * r1 + r2_ * r2_;
                         const float ril = rsqrtf(lr2);
                         const float lr = lr2 * ril;
                         const float qref = ei.x * (ei.y - ril);
-                        const float h = 2.f * (r0 * e0 + r1 * e1 + r2 * e2) + (e0 * e0 + e1 * e1 + e2 * e2);
+                        const float h = 2.f * (r0 * e0 + r1 * e1 + r2_ * e2) + (e0 * e0 + e1 * e1 + e2 * e2);
                         const float rl = rsqrtf(lr2 + h);
                         const float l = (lr2 + h) * rl;
                         const float dq = __fdividef(ei.x * h * rl * ril, l + lr);
                         g0 += qref * e0 + dq * (r0 + e0);
                         g1 += qref * e1 + dq * (r1 + e1);
-                        g2 += qref * e2 + dq * (r2 + e2);
+                        g2 += qref * e2 + dq * (r2_ + e2);
                     }
                     const float im = imh[i];
                     float w0 = vh[i], w1 = vh[n + i], w2 = vh[2 * n + i];
@@ -415,14 +518,9 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
                     if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
                 }
             }
-            // publish this iteration's partials; tested after the next barrier
-            publish(sh, pt, rs, kes, want_k, rb);
-            rbp = rb;
-            rb ^= 1;
-            pending = true;
-            ++it;
+            // publish this evaluation's partials; tested two iterations later
+            publish(sh, pt, rs, kes, want_k, b);
             ++since;
-            b ^= 1;
         }
     }
 
@@ -487,39 +585,42 @@ __device__ void solve_rve_mixed(cg::cluster_group &cl, MixedShared &sh, const De
         O.iters[p] = it;
         O.rel_res[p] = f_ref > 0.0 ? r / f_ref : (r > 0.0 ? INFINITY : 0.0);
         O.status[p] = status;
-        O.f_ref[p] = f_ref;
         O.ke[p] = want_k ? df_to_double(k2) : 0.0;
-        O.lead[p] = lead;
     }
     cl.sync();
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(512) dr_mixed_kernel(DevMesh M, DevState S, DevResults O,
-                                                       SolveParams P, int part_cap) {
+__global__ void __launch_bounds__(256) dr_mixed_lead_kernel(DevMesh M, DevState S, DevResults O,
+                                                            SolveParams P, int part_cap) {
     extern __shared__ __align__(16) float4 dsm[];
     __shared__ MixedShared sh;
     cg::cluster_group cl = cg::this_cluster();
-    const int C = (int)cl.num_blocks();
-    float4 *Pl = dsm, *Q0 = dsm + part_cap, *Q1 = dsm + 2 * part_cap;
-    if ((int)threadIdx.x < C) {
-        const int r = threadIdx.x;
-        sh.P[r] = cl.map_shared_rank(Pl, r);
-        sh.Q[0][r] = cl.map_shared_rank(Q0, r);
-        sh.Q[1][r] = cl.map_shared_rank(Q1, r);
-        sh.redp[r] = cl.map_shared_rank(&sh.red[0][0][0], r);
-        sh.kredp[r] = cl.map_shared_rank(&sh.kred[0][0][0], r);
-    }
-    if (threadIdx.x == 0) sh.sigp = cl.map_shared_rank(&sh.sig[0][0], 0);
+    float4 *Pl = dsm, *Q0 = dsm + part_cap;
+    float4 *Qb[kBufs] = {Q0, Q0, Q0};
+    map_remote(cl, sh, Pl, Qb, (int)cl.num_blocks());
     int rb = 0;
     for (;;) {
-        if (cl.block_rank() == 0 && threadIdx.x == 0) sh.item = atomicAdd(P.counter, 1);
-        cl.sync();
-        const int item = *cl.map_shared_rank(&sh.item, 0);
-        cl.sync();
+        const int item = next_item(cl, sh, P.counter);
         if (item >= P.queue_len) return;
-        solve_rve_mixed(cl, sh, M, S, O, P, P.queue[item], Pl, Q0, Q1, rb);
+        lead_rve(cl, sh, M, S, O, P, P.queue[item], Pl, Q0, rb);
+    }
+}
+
+__global__ void __launch_bounds__(256, 3) dr_mixed_fp32_kernel(DevMesh M, DevState S, DevResults O,
+                                                               SolveParams P, int part_cap) {
+    extern __shared__ __align__(16) float4 dsm[];
+    __shared__ MixedShared sh;
+    cg::cluster_group cl = cg::this_cluster();
+    float4 *Pl = dsm;
+    float4 *Qb[kBufs] = {dsm + part_cap, dsm + 2 * part_cap, dsm + 3 * part_cap};
+    map_remote(cl, sh, Pl, Qb, (int)cl.num_blocks());
+    int rb = 0;
+    for (;;) {
+        const int item = next_item(cl, sh, P.counter + 1);
+        if (item >= P.queue_len) return;
+        fp32_rve(cl, sh, M, S, O, P, P.queue[item], Pl, Qb, rb);
     }
 }
 
@@ -539,28 +640,45 @@ cudaLaunchConfig_t mixed_config(int clusters, int parts, int block, size_t smem,
     cfg.numAttrs = 1;
     return cfg;
 }
+
+template <class K>
+void prepare(K kernel, size_t smem) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
 }  // namespace
 
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
-                    int clusters, int parts, int block, size_t smem, void *stream) {
-    cudaFuncSetAttribute(dr_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(dr_mixed_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                    int clusters_lead, int clusters_fp32, int parts, int block, size_t smem_lead,
+                    size_t smem_fp32, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg =
-        mixed_config(clusters, parts, block, smem, attr, static_cast<cudaStream_t>(stream));
-    const int part_cap = (int)(smem / (3 * sizeof(float4)));
-    cudaError_t e = cudaLaunchKernelEx(&cfg, dr_mixed_kernel, m, s, r, p, part_cap);
+    prepare(dr_mixed_lead_kernel, smem_lead);
+    cudaLaunchConfig_t cfg = mixed_config(clusters_lead, parts, block, smem_lead, attr, st);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, dr_mixed_lead_kernel, m, s, r, p,
+                                       (int)(smem_lead / (2 * sizeof(float4))));
+    if (e != cudaSuccess) return (int)e;
+    prepare(dr_mixed_fp32_kernel, smem_fp32);
+    cfg = mixed_config(clusters_fp32, parts, block, smem_fp32, attr, st);
+    e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel, m, s, r, p,
+                           (int)(smem_fp32 / ((1 + kBufs) * sizeof(float4))));
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 
-int occupancy_dr_mixed(int parts, int block, size_t smem) {
-    cudaFuncSetAttribute(dr_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(dr_mixed_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+int occupancy_dr_mixed(int lead, int parts, int block, size_t smem) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = mixed_config(parts * 64, parts, block, smem, attr, nullptr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, dr_mixed_kernel, &cfg) != cudaSuccess) {
+    cudaError_t e;
+    if (lead) {
+        prepare(dr_mixed_lead_kernel, smem);
+        e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_lead_kernel, &cfg);
+    } else {
+        prepare(dr_mixed_fp32_kernel, smem);
+        e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_fp32_kernel, &cfg);
+    }
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

@@ -40,10 +40,11 @@ __global__ void k_csr_fill(int64_t n_csr, const int64_t *elem_of, const double *
 // One CTA per RVE: lumped masses m_i = sum_e 1/2 rho A_e L_e with
 // rho A_e = EA_e / L_e^2 (in the node's element order), and the critical step
 // min_e L_e sqrt(rho A_e / EA_e).
-__global__ void k_mass_dt(RveDesc *rve, const int32_t *rowptr, const double *EA_csr,
-                          const double *L_csr, const double *el_EA, const double *el_L,
-                          const double *X0, const double *X1, const double *X2, double *mass,
-                          float *imh, float *iml, float *Xh, float *Xl) {
+__global__ void k_mass_dt(RveDesc *rve, const int32_t *rowptr, const int32_t *col,
+                          const double *EA_csr, const double *L_csr, const double *el_EA,
+                          const double *el_L, const double *X0, const double *X1,
+                          const double *X2, double *mass, float *imh, float *iml, float *Xh,
+                          float *Xl, float4 *dh, float4 *dl) {
     __shared__ double red[32];
     RveDesc &R = rve[blockIdx.x];
     const int32_t *rp = rowptr + R.rp0;
@@ -54,6 +55,18 @@ __global__ void k_mass_dt(RveDesc *rve, const int32_t *rowptr, const double *EA_
             const double L = L_csr[kk];
             const double rhoA = ddiv(EA_csr[kk], dmul(L, L));
             m = dadd(m, dmul(0.5, dmul(rhoA, L)));
+        }
+        // per CSR entry: D = X_j - X_i and the reference length, double-float
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int64_t kk = R.csr0 + k;
+            const int64_t j = R.node0 + col[kk], ii = R.node0 + i;
+            float a0, b0, a1, b1, a2, b2, a3, b3;
+            split_df(dsub(X0[j], X0[ii]), a0, b0);
+            split_df(dsub(X1[j], X1[ii]), a1, b1);
+            split_df(dsub(X2[j], X2[ii]), a2, b2);
+            split_df(L_csr[kk], a3, b3);
+            dh[kk] = make_float4(a0, a1, a2, a3);
+            dl[kk] = make_float4(b0, b1, b2, b3);
         }
         mass[R.node0 + i] = m;
         float h = 0.f, l = 0.f;
@@ -92,8 +105,8 @@ int launch_setup(int32_t n_rve, int64_t n_el, int64_t n_csr, RveDesc *rve,
                  const double *X2, const int64_t *elem_of, const double *EA_csr,
                  const double *el_EA, const int32_t *rowptr, double *el_L, double *L_csr,
                  float2 *eaf, float2 *eaf_lo, double *mass, float *imh, float *iml,
-                 float *Xh, float *Xl, int64_t n_nodes, void *stream) {
-    (void)n_nodes;
+                 float *Xh, float *Xl, const int32_t *col, float4 *dh, float4 *dl,
+                 void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n_el > 0) {
         const int g = (int)((n_el + 255) / 256 < 65535 ? (n_el + 255) / 256 : 65535);
@@ -103,8 +116,8 @@ int launch_setup(int32_t n_rve, int64_t n_el, int64_t n_csr, RveDesc *rve,
         const int g = (int)((n_csr + 255) / 256 < 65535 ? (n_csr + 255) / 256 : 65535);
         k_csr_fill<<<g, 256, 0, st>>>(n_csr, elem_of, el_L, EA_csr, L_csr, eaf, eaf_lo);
     }
-    k_mass_dt<<<n_rve, 256, 0, st>>>(rve, rowptr, EA_csr, L_csr, el_EA, el_L, X0, X1, X2, mass,
-                                     imh, iml, Xh, Xl);
+    k_mass_dt<<<n_rve, 256, 0, st>>>(rve, rowptr, col, EA_csr, L_csr, el_EA, el_L, X0, X1, X2,
+                                     mass, imh, iml, Xh, Xl, dh, dl);
     return (int)cudaGetLastError();
 }
 

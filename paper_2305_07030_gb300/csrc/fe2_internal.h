@@ -56,6 +56,7 @@ struct DevMesh {
     const double *L;              // per CSR entry
     const float2 *eaf;            // per CSR entry: (EA, 1/L) double-float high parts
     const float2 *eaf_lo;         // per CSR entry: low parts
+    const float4 *dh, *dl;        // per CSR entry: (X_j - X_i, L) as double-float hi / lo
     const int32_t *el_a, *el_b;   // stress elements (RVE-local permuted ids)
     const double *el_EA, *el_L;
 };
@@ -94,7 +95,7 @@ struct SolveParams {
     int rebase_every;
     const int32_t *queue; // RVE ids in scheduling order
     int32_t queue_len;
-    int32_t *counter;     // work-queue head (zeroed before the launch)
+    int32_t *counter;     // work-queue heads (zeroed before the launch; mixed uses two)
     int smem_positions;   // FP64 kernel: 1 = positions staged in shared memory
 };
 
@@ -106,16 +107,18 @@ int launch_setup(int32_t n_rve, int64_t n_el, int64_t n_csr, RveDesc *rve,
                  const double *X2, const int64_t *elem_of, const double *EA_csr,
                  const double *el_EA, const int32_t *rowptr, double *el_L, double *L_csr,
                  float2 *eaf, float2 *eaf_lo, double *mass, float *imh, float *iml,
-                 float *Xh, float *Xl, int64_t n_nodes, void *stream);
+                 float *Xh, float *Xl, const int32_t *col, float4 *dh, float4 *dl,
+                 void *stream);
 int launch_dr_fp64(const DevMesh &m, const DevState &s, const DevResults &r,
                    const SolveParams &p, int grid, int block, size_t smem, void *stream);
-// Mixed solver: one thread-block cluster of `parts` CTAs per RVE.
+// Mixed solver: one thread-block cluster of `parts` CTAs per RVE; two
+// persistent launches (double-float lead, then the FP32 phase).
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r,
-                    const SolveParams &p, int clusters, int parts, int block, size_t smem,
-                    void *stream);
+                    const SolveParams &p, int clusters_lead, int clusters_fp32, int parts,
+                    int block, size_t smem_lead, size_t smem_fp32, void *stream);
 // Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.
 int occupancy_dr_fp64(int smem_positions, int block, size_t smem);
-int occupancy_dr_mixed(int parts, int block, size_t smem);
+int occupancy_dr_mixed(int lead, int parts, int block, size_t smem);
 
 // Naive comparator: scratch sized for the largest RVE, and one RVE's solve.
 struct NaiveScratch {

@@ -89,6 +89,7 @@ struct fe2_batch {
     DevBuf<float> d_Xh, d_Xl, d_imh, d_iml;
     DevBuf<int32_t> d_rowptr, d_col, d_col_part, d_part_off, d_el_a, d_el_b;
     DevBuf<float2> d_eaf, d_eaf_lo;
+    DevBuf<float4> d_dh, d_dl;
     DevBuf<double> d_u, d_v, d_a, d_xg;
     DevBuf<float> d_uh, d_ul, d_vh, d_vl, d_ah, d_al, d_fg;
     DevBuf<double> d_F, d_sigma, d_rel, d_fref, d_ke;
@@ -126,6 +127,8 @@ struct fe2_batch {
         m.L = d_L_csr.p;
         m.eaf = d_eaf.p;
         m.eaf_lo = d_eaf_lo.p;
+        m.dh = d_dh.p;
+        m.dl = d_dl.p;
         m.el_a = d_el_a.p;
         m.el_b = d_el_b.p;
         m.el_EA = d_el_EA.p;
@@ -153,7 +156,7 @@ struct fe2_batch {
         d_el_EA.release(); d_el_L.release(); d_Xh.release(); d_Xl.release(); d_imh.release();
         d_iml.release(); d_rowptr.release(); d_col.release(); d_col_part.release();
         d_part_off.release(); d_el_a.release(); d_el_b.release(); d_eaf.release();
-        d_eaf_lo.release(); d_u.release(); d_v.release(); d_a.release(); d_xg.release();
+        d_eaf_lo.release(); d_dh.release(); d_dl.release(); d_u.release(); d_v.release(); d_a.release(); d_xg.release();
         d_uh.release(); d_ul.release(); d_vh.release(); d_vl.release(); d_ah.release();
         d_al.release(); d_fg.release(); d_F.release(); d_sigma.release(); d_rel.release();
         d_fref.release(); d_ke.release(); d_iters.release(); d_lead.release();
@@ -196,12 +199,17 @@ namespace {
 
 bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
+// Shared-memory bytes per staged node of the mixed solver's FP32 kernel
+// (reference position plus three rotating increment buffers, float4 each).
+constexpr size_t kMixedNodeBytes = 64;
+
 // Number of cluster CTAs for an RVE of n nodes in the mixed solver: a power
-// of two with about `target` nodes per CTA, enough parts for the staged
-// positions (48 B per node) to fit in shared memory, at most 16.
+// of two with about `target` nodes per CTA, enough parts for the staged state
+// to fit in shared memory, at most 16.
 int choose_parts(int n, int target, size_t smem_cap) {
     int C = 1;
-    while (C < kMaxParts && ((n + C - 1) / C > target || (size_t)48 * ((n + C - 1) / C + 64) > smem_cap))
+    while (C < kMaxParts &&
+           ((n + C - 1) / C > target || kMixedNodeBytes * ((n + C - 1) / C + 64) > smem_cap))
         C *= 2;
     return C;
 }
@@ -268,7 +276,7 @@ void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
             c.rves.push_back(p);
             c.part_max = std::max(c.part_max, b->rve[p].part_max);
             c.free_max = std::max(c.free_max, b->part_free_max[p]);
-            c.smem_bytes = (size_t)48 * c.part_max;
+            c.smem_bytes = kMixedNodeBytes * c.part_max;
         }
         for (auto &c : cls)
             if (!c.rves.empty()) out.push_back(c);
@@ -481,6 +489,8 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     A(b->d_L_csr.alloc(2 * E), "L_csr");
     A(b->d_eaf.alloc(2 * E), "eaf");
     A(b->d_eaf_lo.alloc(2 * E), "eaf_lo");
+    A(b->d_dh.alloc(2 * E), "dh");
+    A(b->d_dl.alloc(2 * E), "dl");
     A(b->d_col.alloc(2 * E), "col");
     A(b->d_col_part.alloc(2 * E), "col_part");
     A(b->d_rowptr.alloc(N + n_rve), "rowptr");
@@ -535,7 +545,8 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
                                    b->d_X.p + N, b->d_X.p + 2 * N, d_elemof.p, b->d_EA_csr.p,
                                    b->d_el_EA.p, b->d_rowptr.p, b->d_el_L.p, b->d_L_csr.p,
                                    b->d_eaf.p, b->d_eaf_lo.p, b->d_mass.p, b->d_imh.p,
-                                   b->d_iml.p, b->d_Xh.p, b->d_Xl.p, N, st);
+                                   b->d_iml.p, b->d_Xh.p, b->d_Xl.p, b->d_col.p, b->d_dh.p,
+                                   b->d_dl.p, st);
         A((cudaError_t)e, "setup kernels");
     }
     if (rc == FE2_OK)
@@ -594,12 +605,13 @@ fe2_status check_opts(const fe2_opts &o) {
     return FE2_OK;
 }
 
-// Threads per CTA of the mixed solver. A fixed default keeps every RVE's
-// result independent of which other RVEs share its launch (the residual's
-// partial sums follow the thread-to-node mapping).
+// Threads per CTA of the mixed solver (at most 256, the kernels' launch
+// bound). A fixed default keeps every RVE's result independent of which
+// other RVEs share its launch (the residual's partial sums follow the
+// thread-to-node mapping).
 int mixed_block(const SizeClass &c, int requested) {
     (void)c;
-    return requested ? requested : 256;
+    return requested ? std::min(requested, 256) : 256;
 }
 
 fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
@@ -628,7 +640,7 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev[0], 0));
         P.queue = b->d_queue.p + (fp64 ? 0 : b->n_rve) + c.queue_off;
         P.queue_len = (int32_t)c.rves.size();
-        P.counter = b->d_counters.p + k;
+        P.counter = b->d_counters.p + 2 * k;
         P.smem_positions = c.smem_positions;
         CUDA_TRY(cudaEventRecord(b->tev[2 * k], s));
         int e;
@@ -640,12 +652,15 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
             e = launch_dr_fp64(M, S, R, P, grid, block, smem, s);
         } else {
             const int block = mixed_block(c, o.block_threads);
-            const int resident = occupancy_dr_mixed(c.parts, block, c.smem_bytes);
-            if (resident < 1)
+            const size_t smem_lead = c.smem_bytes / 2, smem_fp32 = c.smem_bytes;
+            const int res_lead = occupancy_dr_mixed(1, c.parts, block, smem_lead);
+            const int res_fp32 = occupancy_dr_mixed(0, c.parts, block, smem_fp32);
+            if (res_lead < 1 || res_fp32 < 1)
                 return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
                                            std::to_string(c.smem_bytes) + " B shared memory fits");
-            const int clusters = std::max(1, std::min<int>((int)c.rves.size(), resident));
-            e = launch_dr_mixed(M, S, R, P, clusters, c.parts, block, c.smem_bytes, s);
+            const int nq = (int)c.rves.size();
+            e = launch_dr_mixed(M, S, R, P, std::min(nq, res_lead), std::min(nq, res_fp32), c.parts,
+                                block, smem_lead, smem_fp32, s);
         }
         if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
         CUDA_TRY(cudaEventRecord(b->tev[2 * k + 1], s));
