@@ -649,19 +649,20 @@ void prepare(K kernel, size_t smem) {
 }  // namespace
 
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
-                    int clusters_lead, int clusters_fp32, int parts, int block, size_t smem_lead,
-                    size_t smem_fp32, void *stream) {
+                    int lead, int clusters, int parts, int block, size_t smem, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaLaunchAttribute attr[1];
-    prepare(dr_mixed_lead_kernel, smem_lead);
-    cudaLaunchConfig_t cfg = mixed_config(clusters_lead, parts, block, smem_lead, attr, st);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, dr_mixed_lead_kernel, m, s, r, p,
-                                       (int)(smem_lead / (2 * sizeof(float4))));
-    if (e != cudaSuccess) return (int)e;
-    prepare(dr_mixed_fp32_kernel, smem_fp32);
-    cfg = mixed_config(clusters_fp32, parts, block, smem_fp32, attr, st);
-    e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel, m, s, r, p,
-                           (int)(smem_fp32 / ((1 + kBufs) * sizeof(float4))));
+    cudaLaunchConfig_t cfg = mixed_config(clusters, parts, block, smem, attr, st);
+    cudaError_t e;
+    if (lead) {
+        prepare(dr_mixed_lead_kernel, smem);
+        e = cudaLaunchKernelEx(&cfg, dr_mixed_lead_kernel, m, s, r, p,
+                               (int)(smem / (2 * sizeof(float4))));
+    } else {
+        prepare(dr_mixed_fp32_kernel, smem);
+        e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel, m, s, r, p,
+                               (int)(smem / ((1 + kBufs) * sizeof(float4))));
+    }
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }

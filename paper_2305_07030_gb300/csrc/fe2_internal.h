@@ -112,10 +112,11 @@ int launch_setup(int32_t n_rve, int64_t n_el, int64_t n_csr, RveDesc *rve,
 int launch_dr_fp64(const DevMesh &m, const DevState &s, const DevResults &r,
                    const SolveParams &p, int grid, int block, size_t smem, void *stream);
 // Mixed solver: one thread-block cluster of `parts` CTAs per RVE; two
-// persistent launches (double-float lead, then the FP32 phase).
+// persistent launches per class, the double-float lead (lead = 1) and then
+// the FP32 phase (lead = 0).
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r,
-                    const SolveParams &p, int clusters_lead, int clusters_fp32, int parts,
-                    int block, size_t smem_lead, size_t smem_fp32, void *stream);
+                    const SolveParams &p, int lead, int clusters, int parts, int block,
+                    size_t smem, void *stream);
 // Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.
 int occupancy_dr_fp64(int smem_positions, int block, size_t smem);
 int occupancy_dr_mixed(int lead, int parts, int block, size_t smem);

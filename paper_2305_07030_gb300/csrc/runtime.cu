@@ -576,7 +576,7 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         A(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         if (rc == FE2_OK) b->ev.push_back(e);
     }
-    for (int k = 0; k < 12 && rc == FE2_OK; ++k) {
+    for (int k = 0; k < 24 && rc == FE2_OK; ++k) {
         cudaEvent_t e;
         A(cudaEventCreate(&e), "timing event");
         if (rc == FE2_OK) b->tev.push_back(e);
@@ -633,7 +633,7 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
     const DevResults R = b->results();
     // fork: every class runs on its own stream, concurrently
     CUDA_TRY(cudaEventRecord(b->ev[0], st));
-    int launches = 0;
+    int launches = 0, timed = 0;
     for (size_t k = 0; k < classes.size(); ++k) {
         const SizeClass &c = classes[k];
         cudaStream_t s = b->side[k];
@@ -642,34 +642,43 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
         P.queue_len = (int32_t)c.rves.size();
         P.counter = b->d_counters.p + 2 * k;
         P.smem_positions = c.smem_positions;
-        CUDA_TRY(cudaEventRecord(b->tev[2 * k], s));
-        int e;
+        const int nq = (int)c.rves.size();
         if (fp64) {
             const int block = o.block_threads ? o.block_threads : 512;
             const size_t smem = c.smem_positions ? c.smem_bytes : 0;
             const int per_sm = std::max(1, occupancy_dr_fp64(c.smem_positions, block, smem));
-            const int grid = std::max(1, std::min<int>((int)c.rves.size(), per_sm * b->sm_count));
-            e = launch_dr_fp64(M, S, R, P, grid, block, smem, s);
+            const int grid = std::max(1, std::min<int>(nq, per_sm * b->sm_count));
+            if (timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
+            CUDA_TRY(cudaEventRecord(b->tev[timed], s));
+            const int e = launch_dr_fp64(M, S, R, P, grid, block, smem, s);
+            if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
+            CUDA_TRY(cudaEventRecord(b->tev[timed + 1], s));
+            timed += 2;
+            ++launches;
         } else {
             const int block = mixed_block(c, o.block_threads);
-            const size_t smem_lead = c.smem_bytes / 2, smem_fp32 = c.smem_bytes;
-            const int res_lead = occupancy_dr_mixed(1, c.parts, block, smem_lead);
-            const int res_fp32 = occupancy_dr_mixed(0, c.parts, block, smem_fp32);
-            if (res_lead < 1 || res_fp32 < 1)
-                return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
-                                           std::to_string(c.smem_bytes) + " B shared memory fits");
-            const int nq = (int)c.rves.size();
-            e = launch_dr_mixed(M, S, R, P, std::min(nq, res_lead), std::min(nq, res_fp32), c.parts,
-                                block, smem_lead, smem_fp32, s);
+            for (int lead = 1; lead >= 0; --lead) {
+                const size_t smem = lead ? c.smem_bytes / 2 : c.smem_bytes;
+                const int resident = occupancy_dr_mixed(lead, c.parts, block, smem);
+                if (resident < 1)
+                    return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
+                                               std::to_string(smem) + " B shared memory fits");
+                if (timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
+                CUDA_TRY(cudaEventRecord(b->tev[timed], s));
+                const int e = launch_dr_mixed(M, S, R, P, lead, std::min(nq, resident), c.parts, block,
+                                              smem, s);
+                if (e != 0)
+                    return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
+                CUDA_TRY(cudaEventRecord(b->tev[timed + 1], s));
+                timed += 2;
+                ++launches;
+            }
         }
-        if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
-        CUDA_TRY(cudaEventRecord(b->tev[2 * k + 1], s));
-        ++launches;
         CUDA_TRY(cudaEventRecord(b->ev[1 + k], s));
         CUDA_TRY(cudaStreamWaitEvent(st, b->ev[1 + k], 0));
     }
     b->last_launches = launches;
-    b->last_timed = launches;
+    b->last_timed = timed / 2;
     b->last_stream = st;
     b->solved = true;
     return FE2_OK;
