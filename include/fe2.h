@@ -212,6 +212,53 @@ fe2_status fe2_batch_solve_naive(fe2_batch *b, const double *F, const fe2_opts *
 /* Message of the last failed call on this thread ("" if none). */
 const char *fe2_last_error(void);
 
+/*
+ * Allocation-free solve of ONE RVE. The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc (code running during
+ * CUDA graph capture, real-time loops that must not allocate, frameworks that
+ * own every device allocation through their own pools). It allocates nothing:
+ * inputs and outputs are the caller's DEVICE buffers, and all working memory
+ * is one file-scope device array of fe2_noalloc_scratch_bytes() bytes (about
+ * 1.6 MB) that every GPU loading the library holds until the process exits.
+ *
+ * It runs the same per-RVE FP64 solver as fe2_batch_solve with
+ * FE2_PREC_FP64, so results are bit-identical to that path, in one CTA.
+ *
+ * n_nodes    1 .. 4096 nodes;  n_elems  0 .. 16384 elements (else FE2_EINVAL)
+ * X_dev      3*n_nodes reference coordinates, xyz interleaved
+ * conn_dev   2*n_elems node ids (0 .. n_nodes-1);  EA_dev  n_elems rigidities
+ * fixed_dev  n_nodes flags (non-zero: prescribed x = F X)
+ * F_dev      9 doubles, row-major
+ * damping    c >= 0, or negative for 0.002 (512/n)^(1/3);  V0 > 0
+ * opts       as for fe2_batch_solve; precision must be FE2_PREC_FP64
+ * u_dev      3*n_nodes: read for FE2_INIT_WARM (free nodes), written with
+ *            the final displacement (caller's node order)
+ * sigma_dev (9), iters_dev (1), rel_res_dev (1), status_dev (1): outputs;
+ *            status 4 means the device-side input checks failed (an id out of
+ *            range, a self-loop, a repeated element, a zero length, EA <= 0 or
+ *            a non-finite value) and nothing was solved.
+ * stream     cudaStream_t or NULL. The call is asynchronous on it.
+ *
+ * The scratch array is shared by all calls on a device and keeps the last
+ * call's contents; each solve rewrites or clears everything it reads. Calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it: serialise them. The first call on a device looks up the array's device
+ * address (and sets the kernel's shared-memory limit); make that first call
+ * before any stream capture.
+ */
+fe2_status fe2_rve_solve_noalloc(int32_t n_nodes, int32_t n_elems, const double *X_dev,
+                                 const int32_t *conn_dev, const double *EA_dev,
+                                 const uint8_t *fixed_dev, const double *F_dev, double damping,
+                                 double V0, const fe2_opts *opts, double *u_dev, double *sigma_dev,
+                                 int64_t *iters_dev, double *rel_res_dev, int32_t *status_dev,
+                                 void *stream);
+
+/* Size in bytes of the allocation-free entry point's device scratch array. */
+size_t fe2_noalloc_scratch_bytes(void);
+
+/* Message of the last failed fe2_rve_solve_noalloc call on this thread. */
+const char *fe2_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

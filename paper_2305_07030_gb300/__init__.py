@@ -58,6 +58,13 @@ def _load():
     lib.fe2_batch_parts.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.restype = C.c_int
+    lib.fe2_rve_solve_noalloc.argtypes = [I32, I32, P, P, P, P, P, D, D, C.POINTER(Opts), P, P, P,
+                                          P, P, P]
+    lib.fe2_rve_solve_noalloc.restype = C.c_int
+    lib.fe2_noalloc_scratch_bytes.argtypes = []
+    lib.fe2_noalloc_scratch_bytes.restype = C.c_size_t
+    lib.fe2_noalloc_last_error.argtypes = []
+    lib.fe2_noalloc_last_error.restype = C.c_char_p
     lib.fe2_last_error.argtypes = []
     lib.fe2_last_error.restype = C.c_char_p
     for name in ("fe2_batch_create", "fe2_batch_solve", "fe2_batch_solve_dev",
@@ -79,6 +86,22 @@ def probe_smem_bandwidth():
     if rc != 0:
         raise FE2Error(3, f"smem probe failed ({rc})")
     return g.value, c.value
+
+
+def rve_solve_noalloc(n_nodes, n_elems, X_dev, conn_dev, EA_dev, fixed_dev, F_dev, u_dev,
+                      sigma_dev, iters_dev, rel_res_dev, status_dev, damping=-1.0, V0=1.0,
+                      stream=None, **opts):
+    """fe2_rve_solve_noalloc on CUDA tensors (all device buffers are the
+    caller's; the library allocates nothing). Asynchronous on `stream`."""
+    o = make_opts(**opts)
+    dp = lambda t: C.c_void_p(t.data_ptr())  # noqa: E731
+    rc = _lib.fe2_rve_solve_noalloc(int(n_nodes), int(n_elems), dp(X_dev), dp(conn_dev),
+                                    dp(EA_dev), dp(fixed_dev), dp(F_dev), float(damping),
+                                    float(V0), C.byref(o), dp(u_dev), dp(sigma_dev),
+                                    dp(iters_dev), dp(rel_res_dev), dp(status_dev),
+                                    _stream_handle(stream))
+    if rc != 0:
+        raise FE2Error(rc, _lib.fe2_noalloc_last_error().decode())
 
 
 def last_error() -> str:
