@@ -104,10 +104,13 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     w = WORKLOADS[args.workload]()
+    if args.rves:
+        w = w.subset([int(x) for x in args.rves.split(",")])
     nets = w.nets
     P = len(nets)
     batch = fe2.Batch(nets, damping=w.damping)
-    opts = dict(precision=args.precision, init="affine", tol=1e-8)
+    opts = dict(precision=args.precision, init="affine", tol=1e-8, max_iter=args.max_iter,
+                lead_iters=args.lead_iters)
     F_host = np.ascontiguousarray(w.F.reshape(P, 9))
     F_dev = torch.tensor(F_host.reshape(-1), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -142,7 +145,7 @@ def run_ours(args, rank, world):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
-            kernel_ms.append(max(batch.kernel_times_ms()))
+            kernel_ms.append(batch.kernel_times_ms())
             iters_all.append(it_dev.cpu().numpy().copy())
         # end-to-end through the public API with host buffers: H2D of F from
         # pinned memory and D2H of the stresses inside the timed region
@@ -174,15 +177,21 @@ def run_ours(args, rank, world):
         fx = n.fixed.astype(bool)
         deg = np.bincount(n.elems.ravel(), minlength=n.n_nodes)
         stats.append((int((~fx).sum()), int(deg[~fx].sum())))
-    leads = [int(1000.0 * (n / 512.0) ** (1.0 / 3.0)) for n in nn]
+    # Algorithmic shared-memory bytes of the dominant kernel per launch: the FP32
+    # kernel reads every neighbour's staged position and increment (32 B per
+    # directed edge) and reads/writes each free node's own (48 B); the FP64
+    # kernel reads 24 B per edge and writes 24 B per free node.
+    leads = batch.diagnostics()["lead_iters"] if args.precision == "mixed" else np.zeros(P, int)
     if args.precision == "fp64":
-        alg = sum(it * (24.0 * nnz + 24.0 * nf) for (nf, nnz), it in zip(stats, iters))
+        alg = sum(int(it) * (24.0 * nnz + 24.0 * nf) for (nf, nnz), it in zip(stats, iters))
+        kms = statistics.mean(k[0] for k in kernel_ms)
+        kname = "dr_fp64_kernel"
     else:
-        alg = 0.0
-        for (nf, nnz), it, ld in zip(stats, iters, leads):
-            l = min(int(it), ld)
-            alg += l * (24.0 * nnz + 24.0 * nf) + (int(it) - l) * (32.0 * nnz + 48.0 * nf)
-    kms = statistics.mean(kernel_ms)
+        alg = sum((int(it) - int(ld)) * (32.0 * nnz + 48.0 * nf)
+                  for (nf, nnz), it, ld in zip(stats, iters, leads))
+        kms = statistics.mean(k[1] for k in kernel_ms)  # [lead, fp32] per step
+        kname = "dr_mixed_fp32_kernel"
+    lead_ms = statistics.mean(k[0] for k in kernel_ms) if args.precision == "mixed" else 0.0
     smem_gbs, _ = fe2.probe_smem_bandwidth()
     achieved = alg / (kms * 1e-3) / 1e9
     value = world * P / mean_step
@@ -210,7 +219,8 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "roofline": {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s",
                      "frac": achieved / smem_gbs, "traffic": None,
-                     "kernel": f"dr_{args.precision}_kernel", "kernel_ms": kms,
+                     "kernel": kname, "kernel_ms": kms, "lead_kernel_ms": lead_ms,
+                     "lead_iters_mean": float(np.mean(leads)),
                      "peak_source": "measured live: fe2_probe_smem_bandwidth (float4 shared-memory "
                                     "reads on every SM)"},
         "clocks": clocks,
@@ -334,6 +344,9 @@ def main():
     ap.add_argument("--no-naive", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--rves", default="", help="comma-separated RVE subset (profiling runs)")
+    ap.add_argument("--max-iter", type=int, default=10_000_000)
+    ap.add_argument("--lead-iters", type=int, default=-1)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -51,8 +51,9 @@ constexpr int kMaxWarps = 16;  // blocks of at most 512 threads
 constexpr int kBufs = 3;       // rotating increment / partial buffers
 
 struct MixedShared {
-    float red[kBufs][kMaxParts][kMaxWarps];   // per-warp residual partials of every CTA
-    float kred[kBufs][kMaxParts][kMaxWarps];  // kinetic-energy partials
+    float red[kBufs][kMaxParts * kMaxWarps];  // per-warp residual partials of every CTA,
+                                              // dense: entry (rank * warps + warp)
+    float kred[kBufs][kMaxParts * kMaxWarps]; // kinetic-energy partials
     double sig[kMaxParts][9];                 // stress partials, read by rank 0
     double wsum[kMaxWarps][9];                // per-warp stress partials
     float4 *P[kMaxParts];                     // every CTA's position array
@@ -98,12 +99,11 @@ __device__ __forceinline__ void cluster_wait() {
 // fixed, so every warp of every CTA obtains the same bits. GB300 issues FP64
 // at a small fraction of its FP32 rate, which would make an FP64 reduction by
 // every thread cost more than the iteration itself.
-__device__ __forceinline__ df cluster_total(const float (*red)[kMaxParts][kMaxWarps], int buf, int C) {
-    const int nw = (blockDim.x + 31) >> 5;
-    const int total = C * nw;
+__device__ __forceinline__ df cluster_total(const float (*red)[kMaxParts * kMaxWarps], int buf, int C) {
+    const int total = C * (int)(blockDim.x >> 5);
     const int lane = threadIdx.x & 31;
     df acc = df_from(0.f);
-    for (int j = lane; j < total; j += 32) acc = df_add_f(acc, red[buf][j / nw][j % nw]);
+    for (int j = lane; j < total; j += 32) acc = df_add_f(acc, red[buf][j]);
     for (int o = 16; o > 0; o >>= 1) {
         const df other = {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
         acc = df_add(acc, other);
@@ -121,9 +121,10 @@ __device__ __forceinline__ void publish(MixedShared &sh, const Part &pt, float v
     if (want_k)
         for (int o = 16; o > 0; o >>= 1) kv += __shfl_xor_sync(0xffffffffu, kv, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = buf * (kMaxParts * kMaxWarps) + pt.me * (int)(blockDim.x >> 5) + warp;
     if (lane < pt.C) {
-        sh.redp[lane][(buf * kMaxParts + pt.me) * kMaxWarps + warp] = v;
-        if (want_k) sh.kredp[lane][(buf * kMaxParts + pt.me) * kMaxWarps + warp] = kv;
+        sh.redp[lane][slot] = v;
+        if (want_k) sh.kredp[lane][slot] = kv;
     }
 }
 
@@ -173,8 +174,8 @@ __device__ __forceinline__ void map_remote(cg::cluster_group &cl, MixedShared &s
         const int r = threadIdx.x;
         sh.P[r] = cl.map_shared_rank(Pl, r);
         for (int b = 0; b < kBufs; ++b) sh.Q[b][r] = cl.map_shared_rank(Qb[b], r);
-        sh.redp[r] = cl.map_shared_rank(&sh.red[0][0][0], r);
-        sh.kredp[r] = cl.map_shared_rank(&sh.kred[0][0][0], r);
+        sh.redp[r] = cl.map_shared_rank(&sh.red[0][0], r);
+        sh.kredp[r] = cl.map_shared_rank(&sh.kred[0][0], r);
     }
     if (threadIdx.x == 0) sh.sigp = cl.map_shared_rank(&sh.sig[0][0], 0);
 }
@@ -380,9 +381,12 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         cl.sync();
         const int64_t first = it;  // evaluation index of the first FP32 iteration
         int64_t chk = first;       // next evaluation whose residual is still untested
+        int chkb = 0;              // its buffer
         int since = 0;
-        for (int64_t nidx = first;; ++nidx) {
-            const int b = (int)(nidx % kBufs), bp = (int)((nidx + kBufs - 1) % kBufs);
+        const int32_t *colp = M.col_part + R.csr0;
+        const float2 *eafp = M.eaf + R.csr0;
+        int b = 0, bp = kBufs - 1;  // buffers of evaluation nidx and nidx - 1
+        for (int64_t nidx = first;; ++nidx, bp = b, b = (b + 1 == kBufs ? 0 : b + 1)) {
             // partial velocity update; displacement increment into buffer b
             {
                 const float4 *prev = Qb[bp];
@@ -401,14 +405,15 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             // residual test of evaluation nidx-2 while the barrier completes
             bool stop = false;
             if (chk <= nidx - 2) {
-                r2 = cluster_total(sh.red, (int)(chk % kBufs), pt.C);
-                if (want_k) k2 = cluster_total(sh.kred, (int)(chk % kBufs), pt.C);
+                r2 = cluster_total(sh.red, chkb, pt.C);
+                if (want_k) k2 = cluster_total(sh.kred, chkb, pt.C);
                 const int64_t done = chk + 1;
                 if (!isfinite(r2.hi)) { status = RVE_NAN; stop = true; }
                 else if (df_le(r2, thresh2)) { status = RVE_OK; stop = true; }
                 else if (done >= P.max_iter) { status = RVE_MAXITER; stop = true; }
-                if (stop) { fin = (int)(chk % kBufs); it = done; }
+                if (stop) { fin = chkb; it = done; }
                 ++chk;
+                chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
             }
             cluster_wait();
             if (stop) break;
@@ -417,14 +422,15 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             if (since >= K) {
                 // the reference moves: every earlier evaluation must be tested first
                 if (chk == nidx - 1) {
-                    r2 = cluster_total(sh.red, (int)(chk % kBufs), pt.C);
-                    if (want_k) k2 = cluster_total(sh.kred, (int)(chk % kBufs), pt.C);
+                    r2 = cluster_total(sh.red, chkb, pt.C);
+                    if (want_k) k2 = cluster_total(sh.kred, chkb, pt.C);
                     const int64_t done = chk + 1;
                     if (!isfinite(r2.hi)) { status = RVE_NAN; stop = true; }
                     else if (df_le(r2, thresh2)) { status = RVE_OK; stop = true; }
                     else if (done >= P.max_iter) { status = RVE_MAXITER; stop = true; }
-                    if (stop) { fin = (int)(chk % kBufs); it = done; }
+                    if (stop) { fin = chkb; it = done; }
                     ++chk;
+                    chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
                 }
                 if (stop) break;
                 // fold the increment into the double-float displacement; stage
@@ -486,10 +492,9 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     float g0 = fg[i], g1 = fg[n + i], g2 = fg[2 * n + i];
                     const int beg = rowptr[i], end = rowptr[i + 1];
                     for (int e = beg; e < end; ++e) {
-                        const int64_t kk = R.csr0 + e;
-                        const int cp = M.col_part[kk];
+                        const int cp = colp[e];
                         const int rr = cp >> 16, loc = cp & 0xffff;
-                        const float2 ei = M.eaf[kk];
+                        const float2 ei = eafp[e];
                         const float4 pj = rr == pt.me ? Pl[loc] : sh.P[rr][loc];
                         const float4 qj = rr == pt.me ? cur[loc] : sh.Q[b][rr][loc];
                         const float r0 = pj.x - pi.x, r1 = pj.y - pi.y, r2_ = pj.z - pi.z;
