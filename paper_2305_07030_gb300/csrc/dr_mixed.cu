@@ -49,6 +49,9 @@ namespace {
 
 constexpr int kMaxWarps = 16;  // blocks of at most 512 threads
 constexpr int kBufs = 3;       // rotating increment / partial buffers
+// FP32 kernel shared memory per staged node: reference position, three
+// increment buffers (float4 each), velocity + a.x (float4), a.yz (float2).
+constexpr size_t kFp32NodeBytes = (1 + kBufs + 1) * sizeof(float4) + sizeof(float2);
 
 struct MixedShared {
     float red[kBufs][kMaxParts * kMaxWarps];  // per-warp residual partials of every CTA,
@@ -340,7 +343,7 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
 // ---------------------------------------------------------------------------
 __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
                          const DevResults &O, const SolveParams &P, int p, float4 *Pl,
-                         float4 *const *Qb, int &rb) {
+                         float4 *const *Qb, float4 *SV, float2 *SA, int &rb) {
     const RveDesc R = M.rve[p];
     const Part pt = make_part(M, R, p, (int)cl.block_rank(), (int)cl.num_blocks());
     const int n = R.n_nodes, m = pt.m();
@@ -377,6 +380,12 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                 xr[c] = df_add({Xh[c * n + i], Xl[c * n + i]}, {uh[c * n + i], ul[c * n + i]}).hi;
             Pl[k] = make_float4(xr[0], xr[1], xr[2], 0.f);
             for (int b = 0; b < kBufs; ++b) Qb[b][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            // velocity and acceleration of own free nodes live in shared memory
+            // (rewritten every iteration; global stores would miss L1 each time)
+            if (k < pt.nfr) {
+                SV[k] = make_float4(vh[i], vh[n + i], vh[2 * n + i], ah[i]);
+                SA[k] = make_float2(ah[n + i], ah[2 * n + i]);
+            }
         }
         cl.sync();
         const int64_t first = it;  // evaluation index of the first FP32 iteration
@@ -392,11 +401,13 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                 const float4 *prev = Qb[bp];
                 float4 *cur = Qb[b];
                 for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
-                    const int i = pt.f0 + k;
-                    const float w0 = vh[i] + hdtf * ah[i];
-                    const float w1 = vh[n + i] + hdtf * ah[n + i];
-                    const float w2 = vh[2 * n + i] + hdtf * ah[2 * n + i];
-                    vh[i] = w0; vh[n + i] = w1; vh[2 * n + i] = w2;
+                    float4 va = SV[k];
+                    const float2 a12 = SA[k];
+                    const float w0 = va.x + hdtf * va.w;
+                    const float w1 = va.y + hdtf * a12.x;
+                    const float w2 = va.z + hdtf * a12.y;
+                    va.x = w0; va.y = w1; va.z = w2;
+                    SV[k] = va;
                     const float4 d = nidx == first ? make_float4(0.f, 0.f, 0.f, 0.f) : prev[k];
                     cur[k] = make_float4(d.x + dtf * w0, d.y + dtf * w1, d.z + dtf * w2, 0.f);
                 }
@@ -471,18 +482,15 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                 for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
                     const int i = pt.f0 + k;
                     const float im = imh[i];
-                    float vv = 0.f;
-                    for (int c = 0; c < 3; ++c) {
-                        const float g = fg[c * n + i];
-                        float w = vh[c * n + i];
-                        const float a = g * im - cf * w;
-                        w += hdtf * a;
-                        ah[c * n + i] = a;
-                        vh[c * n + i] = w;
-                        rs += g * g;
-                        vv += w * w;
-                    }
-                    if (want_k) kes += 0.5f * vv / im;
+                    const float4 va = SV[k];
+                    const float g0 = fg[i], g1 = fg[n + i], g2 = fg[2 * n + i];
+                    const float a0 = g0 * im - cf * va.x, a1 = g1 * im - cf * va.y,
+                                a2 = g2 * im - cf * va.z;
+                    const float w0 = va.x + hdtf * a0, w1 = va.y + hdtf * a1, w2 = va.z + hdtf * a2;
+                    SV[k] = make_float4(w0, w1, w2, a0);
+                    SA[k] = make_float2(a1, a2);
+                    rs += g0 * g0 + g1 * g1 + g2 * g2;
+                    if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
                 }
                 since = 0;
             } else {
@@ -512,13 +520,14 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                         g2 += qref * e2 + dq * (r2_ + e2);
                     }
                     const float im = imh[i];
-                    float w0 = vh[i], w1 = vh[n + i], w2 = vh[2 * n + i];
+                    const float4 va = SV[k];
+                    float w0 = va.x, w1 = va.y, w2 = va.z;
                     const float a0 = g0 * im - cf * w0;
                     const float a1 = g1 * im - cf * w1;
                     const float a2 = g2 * im - cf * w2;
                     w0 += hdtf * a0; w1 += hdtf * a1; w2 += hdtf * a2;
-                    ah[i] = a0; ah[n + i] = a1; ah[2 * n + i] = a2;
-                    vh[i] = w0; vh[n + i] = w1; vh[2 * n + i] = w2;
+                    SV[k] = make_float4(w0, w1, w2, a0);
+                    SA[k] = make_float2(a1, a2);
                     rs += g0 * g0 + g1 * g1 + g2 * g2;
                     if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
                 }
@@ -620,12 +629,14 @@ __global__ void __launch_bounds__(256, 3) dr_mixed_fp32_kernel(DevMesh M, DevSta
     cg::cluster_group cl = cg::this_cluster();
     float4 *Pl = dsm;
     float4 *Qb[kBufs] = {dsm + part_cap, dsm + 2 * part_cap, dsm + 3 * part_cap};
+    float4 *SV = dsm + 4 * part_cap;
+    float2 *SA = reinterpret_cast<float2 *>(dsm + 5 * part_cap);
     map_remote(cl, sh, Pl, Qb, (int)cl.num_blocks());
     int rb = 0;
     for (;;) {
         const int item = next_item(cl, sh, P.counter + 1);
         if (item >= P.queue_len) return;
-        fp32_rve(cl, sh, M, S, O, P, P.queue[item], Pl, Qb, rb);
+        fp32_rve(cl, sh, M, S, O, P, P.queue[item], Pl, Qb, SV, SA, rb);
     }
 }
 
@@ -666,7 +677,7 @@ int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, co
     } else {
         prepare(dr_mixed_fp32_kernel, smem);
         e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel, m, s, r, p,
-                               (int)(smem / ((1 + kBufs) * sizeof(float4))));
+                               (int)(smem / kFp32NodeBytes));
     }
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();

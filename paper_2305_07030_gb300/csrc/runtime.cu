@@ -107,6 +107,12 @@ struct fe2_batch {
     std::vector<cudaEvent_t> tev;         // timing events around each class launch
     double *h_F = nullptr;                // pinned staging for F
     cudaEvent_t ev_F = nullptr;           // completion of the last F upload
+    // cost-ordered queues from the previous solve's iteration counts
+    cudaStream_t aux = nullptr;           // private stream for small copies
+    cudaEvent_t ev_done = nullptr;        // end of the last batched solve
+    int64_t *h_iters = nullptr;           // pinned
+    int32_t *h_queue = nullptr;           // pinned, 2 * n_rve
+    bool iters_known = false;
 
     DevMesh mesh() const {
         DevMesh m;
@@ -165,6 +171,14 @@ struct fe2_batch {
         h_F = nullptr;
         if (ev_F) cudaEventDestroy(ev_F);
         ev_F = nullptr;
+        if (aux) cudaStreamDestroy(aux);
+        aux = nullptr;
+        if (ev_done) cudaEventDestroy(ev_done);
+        ev_done = nullptr;
+        if (h_iters) cudaFreeHost(h_iters);
+        h_iters = nullptr;
+        if (h_queue) cudaFreeHost(h_queue);
+        h_queue = nullptr;
         for (auto s : side) cudaStreamDestroy(s);
         for (auto e : ev) cudaEventDestroy(e);
         for (auto e : tev) cudaEventDestroy(e);
@@ -200,8 +214,11 @@ namespace {
 bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
 // Shared-memory bytes per staged node of the mixed solver's FP32 kernel
-// (reference position plus three rotating increment buffers, float4 each).
-constexpr size_t kMixedNodeBytes = 64;
+// (reference position and three rotating increment buffers, float4 each;
+// velocity and acceleration, float4 + float2) and of its lead kernel
+// (double-float displacement, two float4).
+constexpr size_t kMixedNodeBytes = 88;
+constexpr size_t kLeadNodeBytes = 32;
 
 // Number of cluster CTAs for an RVE of n nodes in the mixed solver: a power
 // of two with about `target` nodes per CTA, enough parts for the staged state
@@ -565,6 +582,10 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         A(cudaMemcpy(b->d_queue.p, q.data(), sizeof(int32_t) * 2 * n_rve, cudaMemcpyHostToDevice), "queue");
         A(cudaMallocHost(&b->h_F, sizeof(double) * 9 * n_rve), "pinned F");
         A(cudaEventCreateWithFlags(&b->ev_F, cudaEventDisableTiming), "F event");
+        A(cudaMallocHost(&b->h_iters, sizeof(int64_t) * n_rve), "pinned iters");
+        A(cudaMallocHost(&b->h_queue, sizeof(int32_t) * 2 * n_rve), "pinned queue");
+        A(cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking), "aux stream");
+        A(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming), "done event");
     }
     for (int k = 0; k < 6 && rc == FE2_OK; ++k) {
         cudaStream_t s;
@@ -614,9 +635,38 @@ int mixed_block(const SizeClass &c, int requested) {
     return requested ? std::min(requested, 256) : 256;
 }
 
+// Longest-processing-time order from measured cost: once a solve has
+// finished, its iteration counts (times free nodes) reorder every class's
+// queue so that the slowest RVEs of the next solve start first. Results do not
+// depend on the order; only the tail of the launch does.
+fe2_status reorder_queues(fe2_batch *b) {
+    if (!b->solved || cudaEventQuery(b->ev_done) != cudaSuccess) {
+        cudaGetLastError();  // clear a cudaErrorNotReady
+        return FE2_OK;
+    }
+    const int32_t P = b->n_rve;
+    CUDA_TRY(cudaMemcpyAsync(b->h_iters, b->d_iters.p, sizeof(int64_t) * P, cudaMemcpyDeviceToHost, b->aux));
+    CUDA_TRY(cudaStreamSynchronize(b->aux));
+    auto cost = [&](int32_t p) { return (double)std::max<int64_t>(1, b->h_iters[p]) * (b->rve[p].n_free + 1); };
+    for (int which = 0; which < 2; ++which) {
+        auto &classes = which == 0 ? b->classes_fp64 : b->classes_mixed;
+        for (auto &c : classes) {
+            std::stable_sort(c.rves.begin(), c.rves.end(), [&](int32_t x, int32_t y) { return cost(x) > cost(y); });
+            std::copy(c.rves.begin(), c.rves.end(), b->h_queue + which * P + c.queue_off);
+        }
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->d_queue.p, b->h_queue, sizeof(int32_t) * 2 * P, cudaMemcpyHostToDevice, b->aux));
+    CUDA_TRY(cudaStreamSynchronize(b->aux));
+    return FE2_OK;
+}
+
 fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
     const bool fp64 = o.precision == FE2_PREC_FP64;
     auto &classes = fp64 ? b->classes_fp64 : b->classes_mixed;
+    {
+        const fe2_status r = reorder_queues(b);
+        if (r != FE2_OK) return r;
+    }
     CUDA_TRY(cudaMemsetAsync(b->d_counters.p, 0, sizeof(int32_t) * 32, st));
     SolveParams P;
     P.F = b->d_F.p;
@@ -658,7 +708,7 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
         } else {
             const int block = mixed_block(c, o.block_threads);
             for (int lead = 1; lead >= 0; --lead) {
-                const size_t smem = lead ? c.smem_bytes / 2 : c.smem_bytes;
+                const size_t smem = lead ? kLeadNodeBytes * c.part_max : c.smem_bytes;
                 const int resident = occupancy_dr_mixed(lead, c.parts, block, smem);
                 if (resident < 1)
                     return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
@@ -681,6 +731,7 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
     b->last_timed = timed / 2;
     b->last_stream = st;
     b->solved = true;
+    CUDA_TRY(cudaEventRecord(b->ev_done, st));
     return FE2_OK;
 }
 
