@@ -110,7 +110,7 @@ def run_ours(args, rank, world):
     P = len(nets)
     batch = fe2.Batch(nets, damping=w.damping)
     opts = dict(precision=args.precision, init="affine", tol=1e-8, max_iter=args.max_iter,
-                lead_iters=args.lead_iters)
+                lead_iters=args.lead_iters, block_threads=args.block)
     F_host = np.ascontiguousarray(w.F.reshape(P, 9))
     F_dev = torch.tensor(F_host.reshape(-1), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -347,6 +347,7 @@ def main():
     ap.add_argument("--rves", default="", help="comma-separated RVE subset (profiling runs)")
     ap.add_argument("--max-iter", type=int, default=10_000_000)
     ap.add_argument("--lead-iters", type=int, default=-1)
+    ap.add_argument("--block", type=int, default=0, help="threads per CTA (0 = library default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

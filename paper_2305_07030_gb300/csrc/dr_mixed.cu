@@ -338,6 +338,28 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
     cl.sync();
 }
 
+// FP32 increment of one element's force on node i from neighbour j about the
+// reference state: t(d_ref + dd) - t(d_ref) + q_ref dd, accumulated into g.
+// p* hold FP32 reference positions, q* the FP32 displacement increments;
+// ei = (EA, 1/L).
+__device__ __forceinline__ void edge_increment(const float4 &pi, const float4 &qi, const float4 &pj,
+                                               const float4 &qj, float2 ei, float &g0, float &g1,
+                                               float &g2) {
+    const float r0 = pj.x - pi.x, r1 = pj.y - pi.y, r2 = pj.z - pi.z;
+    const float e0 = qj.x - qi.x, e1 = qj.y - qi.y, e2 = qj.z - qi.z;
+    const float lr2 = r0 * r0 + r1 * r1 + r2 * r2;
+    const float ril = rsqrtf(lr2);
+    const float lr = lr2 * ril;
+    const float qref = ei.x * (ei.y - ril);
+    const float h = 2.f * (r0 * e0 + r1 * e1 + r2 * e2) + (e0 * e0 + e1 * e1 + e2 * e2);
+    const float rl = rsqrtf(lr2 + h);
+    const float l = (lr2 + h) * rl;
+    const float dq = __fdividef(ei.x * h * rl * ril, l + lr);
+    g0 += qref * e0 + dq * (r0 + e0);
+    g1 += qref * e1 + dq * (r1 + e1);
+    g2 += qref * e2 + dq * (r2 + e2);
+}
+
 // ---------------------------------------------------------------------------
 // FP32 kernel: increment iterations, reference refreshes, final state, stress
 // ---------------------------------------------------------------------------
@@ -371,6 +393,9 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         const double dt64 = dmul(P.alpha, R.dtc);
         const float dtf = (float)dt64, hdtf = (float)dmul(0.5, dt64), cf = (float)R.c;
         const int K = P.rebase_every > 0 ? P.rebase_every : 512;
+        // lanes per node: as many as the CTA size allows for this RVE's largest part
+        int lanes = 1;
+        while (lanes < 4 && (int)blockDim.x >= 2 * lanes * R.part_free_max) lanes *= 2;
         // x_ref = X + u (FP32 rounding of the double-float sum), increments zero;
         // g_ref = fg from the lead's last force evaluation at exactly this state
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
@@ -494,42 +519,60 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                 }
                 since = 0;
             } else {
-                for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
-                    const int i = pt.f0 + k;
-                    const float4 pi = Pl[k], qi = cur[k];
-                    float g0 = fg[i], g1 = fg[n + i], g2 = fg[2 * n + i];
-                    const int beg = rowptr[i], end = rowptr[i + 1];
-                    for (int e = beg; e < end; ++e) {
-                        const int cp = colp[e];
-                        const int rr = cp >> 16, loc = cp & 0xffff;
-                        const float2 ei = eafp[e];
-                        const float4 pj = rr == pt.me ? Pl[loc] : sh.P[rr][loc];
-                        const float4 qj = rr == pt.me ? cur[loc] : sh.Q[b][rr][loc];
-                        const float r0 = pj.x - pi.x, r1 = pj.y - pi.y, r2_ = pj.z - pi.z;
-                        const float e0 = qj.x - qi.x, e1 = qj.y - qi.y, e2 = qj.z - qi.z;
-                        const float lr2 = r0 * r0 + r1 * r1 + r2_ * r2_;
-                        const float ril = rsqrtf(lr2);
-                        const float lr = lr2 * ril;
-                        const float qref = ei.x * (ei.y - ril);
-                        const float h = 2.f * (r0 * e0 + r1 * e1 + r2_ * e2) + (e0 * e0 + e1 * e1 + e2 * e2);
-                        const float rl = rsqrtf(lr2 + h);
-                        const float l = (lr2 + h) * rl;
-                        const float dq = __fdividef(ei.x * h * rl * ril, l + lr);
-                        g0 += qref * e0 + dq * (r0 + e0);
-                        g1 += qref * e1 + dq * (r1 + e1);
-                        g2 += qref * e2 + dq * (r2_ + e2);
+                // L lanes share a node's edges (lane s takes edges s, s+L, ...,
+                // two at a time) and combine with shuffles; L is fixed per RVE so
+                // its result does not depend on the launch it runs in.
+                const int L = lanes;
+                const int sub = threadIdx.x & (L - 1), grp = threadIdx.x / L, ngrp = blockDim.x / L;
+                for (int kb = 0; kb < pt.nfr; kb += ngrp) {
+                    const int k = kb + grp;
+                    const bool valid = k < pt.nfr;
+                    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+                    if (valid) {
+                        const int i = pt.f0 + k;
+                        const float4 pi = Pl[k], qi = cur[k];
+                        const int end = rowptr[i + 1];
+                        int e = rowptr[i] + sub;
+                        for (; e + L < end; e += 2 * L) {
+                            const int ca = __ldg(colp + e), cb = __ldg(colp + e + L);
+                            const float2 ea = __ldg(eafp + e), eb = __ldg(eafp + e + L);
+                            const int ra = ca >> 16, la = ca & 0xffff, rb2 = cb >> 16, lb = cb & 0xffff;
+                            const float4 pa = ra == pt.me ? Pl[la] : sh.P[ra][la];
+                            const float4 qa = ra == pt.me ? cur[la] : sh.Q[b][ra][la];
+                            const float4 pb = rb2 == pt.me ? Pl[lb] : sh.P[rb2][lb];
+                            const float4 qb = rb2 == pt.me ? cur[lb] : sh.Q[b][rb2][lb];
+                            edge_increment(pi, qi, pa, qa, ea, g0, g1, g2);
+                            edge_increment(pi, qi, pb, qb, eb, g0, g1, g2);
+                        }
+                        if (e < end) {
+                            const int ca = __ldg(colp + e);
+                            const float2 ea = __ldg(eafp + e);
+                            const int ra = ca >> 16, la = ca & 0xffff;
+                            const float4 pa = ra == pt.me ? Pl[la] : sh.P[ra][la];
+                            const float4 qa = ra == pt.me ? cur[la] : sh.Q[b][ra][la];
+                            edge_increment(pi, qi, pa, qa, ea, g0, g1, g2);
+                        }
                     }
-                    const float im = imh[i];
-                    const float4 va = SV[k];
-                    float w0 = va.x, w1 = va.y, w2 = va.z;
-                    const float a0 = g0 * im - cf * w0;
-                    const float a1 = g1 * im - cf * w1;
-                    const float a2 = g2 * im - cf * w2;
-                    w0 += hdtf * a0; w1 += hdtf * a1; w2 += hdtf * a2;
-                    SV[k] = make_float4(w0, w1, w2, a0);
-                    SA[k] = make_float2(a1, a2);
-                    rs += g0 * g0 + g1 * g1 + g2 * g2;
-                    if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
+                    for (int o = 1; o < L; o <<= 1) {
+                        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+                        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+                        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+                    }
+                    if (valid && sub == 0) {
+                        const int i = pt.f0 + k;
+                        g0 += fg[i]; g1 += fg[n + i]; g2 += fg[2 * n + i];
+                        const float im = imh[i];
+                        const float4 va = SV[k];
+                        float w0 = va.x, w1 = va.y, w2 = va.z;
+                        const float a0 = g0 * im - cf * w0;
+                        const float a1 = g1 * im - cf * w1;
+                        const float a2 = g2 * im - cf * w2;
+                        w0 += hdtf * a0; w1 += hdtf * a1; w2 += hdtf * a2;
+                        SV[k] = make_float4(w0, w1, w2, a0);
+                        SA[k] = make_float2(a1, a2);
+                        rs += g0 * g0 + g1 * g1 + g2 * g2;
+                        if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
+                    }
                 }
             }
             // publish this evaluation's partials; tested two iterations later
@@ -622,7 +665,7 @@ __global__ void __launch_bounds__(256) dr_mixed_lead_kernel(DevMesh M, DevState 
     }
 }
 
-__global__ void __launch_bounds__(256, 3) dr_mixed_fp32_kernel(DevMesh M, DevState S, DevResults O,
+__global__ void __launch_bounds__(512, 1) dr_mixed_fp32_kernel(DevMesh M, DevState S, DevResults O,
                                                                SolveParams P, int part_cap) {
     extern __shared__ __align__(16) float4 dsm[];
     __shared__ MixedShared sh;

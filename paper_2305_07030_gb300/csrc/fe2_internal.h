@@ -37,8 +37,8 @@ struct RveDesc {
     double dtc;       // critical time step (safety factor not applied)
     double c;         // damping coefficient
     double V0;        // reference volume
-    int32_t part_max; // largest part (nodes), sizes the shared memory
-    int32_t pad;
+    int32_t part_max;       // largest part (nodes), sizes the shared memory
+    int32_t part_free_max;  // most free nodes in one part
 };
 
 // Read-only, create-time arrays.

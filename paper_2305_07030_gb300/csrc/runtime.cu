@@ -455,7 +455,7 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         R.c = damping ? damping[p] : 0.002 * std::cbrt(512.0 / (double)n);
         R.V0 = V0 ? V0[p] : 1.0;
         R.part_max = part_max;
-        R.pad = 0;
+        R.part_free_max = free_max;
         b->part_free_max[p] = free_max;
         int32_t pos = 0;
         for (int k = 0; k < n; ++k) {
@@ -626,13 +626,13 @@ fe2_status check_opts(const fe2_opts &o) {
     return FE2_OK;
 }
 
-// Threads per CTA of the mixed solver (at most 256, the kernels' launch
-// bound). A fixed default keeps every RVE's result independent of which
-// other RVEs share its launch (the residual's partial sums follow the
-// thread-to-node mapping).
-int mixed_block(const SizeClass &c, int requested) {
+// Threads per CTA of the mixed solver's FP32 kernel (the lead kernel is
+// bounded to 256). A fixed default keeps every RVE's result independent of
+// which other RVEs share its launch (partial sums follow the thread mapping).
+int mixed_block(const SizeClass &c, int requested, bool lead) {
     (void)c;
-    return requested ? std::min(requested, 256) : 256;
+    const int b = requested ? requested : (lead ? 256 : 512);
+    return lead ? std::min(b, 256) : b;
 }
 
 // Longest-processing-time order from measured cost: once a solve has
@@ -706,8 +706,8 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
             timed += 2;
             ++launches;
         } else {
-            const int block = mixed_block(c, o.block_threads);
             for (int lead = 1; lead >= 0; --lead) {
+                const int block = mixed_block(c, o.block_threads, lead != 0);
                 const size_t smem = lead ? kLeadNodeBytes * c.part_max : c.smem_bytes;
                 const int resident = occupancy_dr_mixed(lead, c.parts, block, smem);
                 if (resident < 1)
