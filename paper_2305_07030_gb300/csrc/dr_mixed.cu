@@ -393,9 +393,13 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         const double dt64 = dmul(P.alpha, R.dtc);
         const float dtf = (float)dt64, hdtf = (float)dmul(0.5, dt64), cf = (float)R.c;
         const int K = P.rebase_every > 0 ? P.rebase_every : 512;
-        // lanes per node: as many as the CTA size allows for this RVE's largest part
+        // lanes per node: as many as the CTA size allows for this RVE's largest part.
+        // Node k's velocity and acceleration are owned by lane 0 of group k in
+        // every phase, so consecutive phases need no barrier between them.
         int lanes = 1;
         while (lanes < 4 && (int)blockDim.x >= 2 * lanes * R.part_free_max) lanes *= 2;
+        const int L = lanes;
+        const int sub = threadIdx.x & (L - 1), grp = threadIdx.x / L, ngrp = blockDim.x / L;
         // x_ref = X + u (FP32 rounding of the double-float sum), increments zero;
         // g_ref = fg from the lead's last force evaluation at exactly this state
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
@@ -425,7 +429,8 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             {
                 const float4 *prev = Qb[bp];
                 float4 *cur = Qb[b];
-                for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+                for (int k = grp; k < pt.nfr; k += ngrp) {
+                    if (sub != 0) continue;
                     float4 va = SV[k];
                     const float2 a12 = SA[k];
                     const float w0 = va.x + hdtf * va.w;
@@ -504,7 +509,8 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     cur[k] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 cl.sync();
-                for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+                for (int k = grp; k < pt.nfr; k += ngrp) {
+                    if (sub != 0) continue;
                     const int i = pt.f0 + k;
                     const float im = imh[i];
                     const float4 va = SV[k];
@@ -522,8 +528,6 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                 // L lanes share a node's edges (lane s takes edges s, s+L, ...,
                 // two at a time) and combine with shuffles; L is fixed per RVE so
                 // its result does not depend on the launch it runs in.
-                const int L = lanes;
-                const int sub = threadIdx.x & (L - 1), grp = threadIdx.x / L, ngrp = blockDim.x / L;
                 for (int kb = 0; kb < pt.nfr; kb += ngrp) {
                     const int k = kb + grp;
                     const bool valid = k < pt.nfr;
