@@ -44,7 +44,8 @@ typedef enum {
     FE2_ECUDA = 3,    /* a CUDA runtime call failed; see fe2_last_error() */
     FE2_ESTATE = 4,   /* call out of order (e.g. results before any solve) */
     FE2_ETIMEOUT = 5, /* a bounded device wait gave up (serving epochs) */
-    FE2_ENODEV = 6    /* no usable sm_103 device */
+    FE2_ENODEV = 6,   /* no usable sm_103 device */
+    FE2_EBUSY = 7     /* every serving slot is in flight; poll and retry */
 } fe2_status;
 
 /* Per-RVE outcome of a solve. */
@@ -173,6 +174,48 @@ fe2_status fe2_batch_diagnostics(fe2_batch *b, double *f_ref, double *kinetic_en
 
 /* Cluster size (CTAs) the MIXED solver uses for each RVE (n_rve entries). */
 fe2_status fe2_batch_parts(const fe2_batch *b, int32_t *parts);
+
+/*
+ * Serving: continuous micro-batching over the RVEs of one batch.
+ *
+ * In the FE2 scheme every macroscale step emits one microscale solve per
+ * material point (Section I), and the paper's motivation is that this loop
+ * runs millions of times per macroscale step (Section III). These calls let
+ * a caller admit solves as they arrive instead of waiting for a whole batch.
+ *
+ * fe2_batch_submit: stage F for the n RVEs `rve_ids` (HOST arrays; 9*n
+ * doubles row-major) and launch the solver for just those RVEs on a stream of
+ * its own, returning at once. Submissions in flight overlap on the device. An
+ * RVE keeps its state on the device, so opts->init = FE2_INIT_WARM restarts
+ * from its last result. FE2_EBUSY when all 8 slots are in flight; FE2_EINVAL
+ * if an id is out of range, repeated, or already in flight.
+ *
+ * fe2_batch_poll: hand back every finished submission that fits in `max`
+ * entries: the RVE ids and, for each, sigma (9), iters, rel_res, status. Any
+ * output pointer except n_out may be NULL. Never blocks.
+ */
+fe2_status fe2_batch_submit(fe2_batch *b, int32_t n, const int32_t *rve_ids, const double *F,
+                            const fe2_opts *opts, int32_t *ticket);
+fe2_status fe2_batch_poll(fe2_batch *b, int32_t max, int32_t *ids, double *sigma, int64_t *iters,
+                          double *rel_res, int32_t *status, int32_t *n_out);
+
+/*
+ * A request loop over a timed schedule (synchronous; returns when every
+ * request has completed). Request r asks for RVE rve[r] with deformation
+ * gradient F[9r..9r+8], arriving at t_arrive[r] seconds after the call (non-
+ * decreasing). A request becomes eligible once it has arrived and the previous
+ * request of the same RVE has completed. Eligible requests are admitted in
+ * micro-batches of at most max_batch RVEs (<= 0: no limit) while a serving
+ * slot is free and the working set of the RVEs in flight stays within
+ * max_inflight_bytes (<= 0: no limit). First solves of an RVE use opts_first;
+ * later ones use opts_next (NULL: opts_first with FE2_INIT_WARM).
+ * Outputs per request: t_done (seconds after the call, when its completion was
+ * observed), and if non-NULL iters, status, sigma (9 per request).
+ */
+fe2_status fe2_serve(fe2_batch *b, int32_t n_req, const int32_t *rve, const double *t_arrive,
+                     const double *F, const fe2_opts *opts_first, const fe2_opts *opts_next,
+                     int32_t max_batch, double max_inflight_bytes, double *t_done, int64_t *iters,
+                     int32_t *status, double *sigma);
 
 /* Copy the current displacement u = x - X (3*N doubles, caller's node order
  * and numbering) to HOST memory. Waits for the last solve. */

@@ -19,7 +19,7 @@ __all__ = ["Batch", "Opts", "last_error", "FE2Error", "LIB_PATH", "RVE_STATUS"]
 LIB_PATH = _build.LIB
 RVE_STATUS = {0: "OK", 1: "MAXITER", 2: "NAN", 3: "PENDING"}
 _STATUS = {0: "FE2_OK", 1: "FE2_EINVAL", 2: "FE2_ENOMEM", 3: "FE2_ECUDA", 4: "FE2_ESTATE",
-           5: "FE2_ETIMEOUT", 6: "FE2_ENODEV"}
+           5: "FE2_ETIMEOUT", 6: "FE2_ENODEV", 7: "FE2_EBUSY"}
 
 
 class FE2Error(RuntimeError):
@@ -55,6 +55,9 @@ def _load():
     lib.fe2_batch_info.argtypes = [P, P, P, P, P]
     lib.fe2_batch_kernel_times.argtypes = [P, P, I32, P]
     lib.fe2_batch_diagnostics.argtypes = [P, P, P, P]
+    lib.fe2_batch_submit.argtypes = [P, I32, P, P, C.POINTER(Opts), P]
+    lib.fe2_batch_poll.argtypes = [P, I32, P, P, P, P, P, P]
+    lib.fe2_serve.argtypes = [P, I32, P, P, P, C.POINTER(Opts), C.POINTER(Opts), I32, D, P, P, P, P]
     lib.fe2_batch_parts.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.restype = C.c_int
@@ -71,7 +74,8 @@ def _load():
                  "fe2_batch_solve_naive", "fe2_batch_stress", "fe2_batch_results_dev",
                  "fe2_batch_get_displacement", "fe2_batch_set_displacement",
                  "fe2_batch_destroy", "fe2_batch_info", "fe2_batch_kernel_times",
-                 "fe2_batch_diagnostics", "fe2_batch_parts"):
+                 "fe2_batch_diagnostics", "fe2_batch_parts", "fe2_batch_submit",
+                 "fe2_batch_poll", "fe2_serve"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -226,6 +230,53 @@ class Batch:
         a, b, c, d = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
         _check(_lib.fe2_batch_info(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
         return {"n_rve": a.value, "n_nodes": b.value, "n_elems": c.value, "launches": d.value}
+
+    # -- serving ---------------------------------------------------------------
+    def submit(self, rve_ids, F, **opts):
+        """Queue a micro-batch for the given RVEs (host arrays); returns its
+        ticket, or None when every slot is busy (FE2_EBUSY)."""
+        ids = np.ascontiguousarray(rve_ids, np.int32)
+        Fh = np.ascontiguousarray(F, np.float64).reshape(len(ids), 9)
+        o = make_opts(**opts)
+        t = C.c_int32(-1)
+        rc = _lib.fe2_batch_submit(self._h, len(ids), _ptr(ids), _ptr(Fh), C.byref(o), C.byref(t))
+        if rc == 7:
+            return None
+        _check(rc)
+        return t.value
+
+    def poll(self):
+        """Results of every finished micro-batch: dict of arrays keyed by field."""
+        P = self.n_rve
+        ids = np.zeros(P, np.int32)
+        sig = np.zeros((P, 9))
+        it = np.zeros(P, np.int64)
+        rr = np.zeros(P)
+        st = np.zeros(P, np.int32)
+        n = C.c_int32(0)
+        _check(_lib.fe2_batch_poll(self._h, P, _ptr(ids), _ptr(sig), _ptr(it), _ptr(rr), _ptr(st),
+                                   C.byref(n)))
+        k = n.value
+        return {"ids": ids[:k], "sigma": sig[:k].reshape(k, 3, 3), "iters": it[:k],
+                "rel_res": rr[:k], "status": [RVE_STATUS[int(x)] for x in st[:k]]}
+
+    def serve(self, rve, t_arrive, F, max_batch=0, max_inflight_bytes=0.0, first=None, next=None):
+        """Run the request loop over a timed schedule; returns per-request
+        completion times (s), iterations, status codes and stresses."""
+        rv = np.ascontiguousarray(rve, np.int32)
+        ta = np.ascontiguousarray(t_arrive, np.float64)
+        Fh = np.ascontiguousarray(F, np.float64).reshape(len(rv), 9)
+        of = make_opts(**(first or {}))
+        on = make_opts(**(next or dict(first or {}, init="warm")))
+        n = len(rv)
+        td = np.zeros(n)
+        it = np.zeros(n, np.int64)
+        st = np.zeros(n, np.int32)
+        sig = np.zeros((n, 9))
+        _check(_lib.fe2_serve(self._h, n, _ptr(rv), _ptr(ta), _ptr(Fh), C.byref(of), C.byref(on),
+                              int(max_batch), float(max_inflight_bytes), _ptr(td), _ptr(it),
+                              _ptr(st), _ptr(sig)))
+        return {"t_done": td, "iters": it, "status": st, "sigma": sig.reshape(n, 3, 3)}
 
     def diagnostics(self):
         P = self.n_rve

@@ -9,12 +9,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/fe2.h"
@@ -66,6 +68,29 @@ struct SizeClass {
     int32_t queue_off = 0;      // offset of its queue in the device queue buffer
 };
 
+// One in-flight micro-batch of the serving interface: its own stream, queue
+// and result staging, so submissions overlap on the device.
+struct ServeSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int32_t *d_ids = nullptr;   // 2 * n_rve: submitted ids, then per-class queues
+    int32_t *d_cnt = nullptr;   // work-queue heads, 2 per class
+    double *d_F = nullptr;      // 9 * n_rve staged deformation gradients
+    double *d_out = nullptr;    // 10 * n_rve: sigma (9) and rel_res per submitted id
+    int64_t *d_it = nullptr;    // n_rve
+    int32_t *d_st = nullptr;    // n_rve
+    int32_t *h_ids = nullptr;   // pinned mirrors
+    double *h_F = nullptr;
+    double *h_out = nullptr;
+    int64_t *h_it = nullptr;
+    int32_t *h_st = nullptr;
+    int n = 0;
+    bool busy = false;
+    double bytes = 0.0;         // working-set bytes it holds (admission)
+};
+
+constexpr int kServeSlots = 8;  // concurrent micro-batches of the serving interface
+
 int env_int(const char *name, int dflt) {
     const char *v = std::getenv(name);
     return v && *v ? std::atoi(v) : dflt;
@@ -113,6 +138,10 @@ struct fe2_batch {
     int64_t *h_iters = nullptr;           // pinned
     int32_t *h_queue = nullptr;           // pinned, 2 * n_rve
     bool iters_known = false;
+    // serving: micro-batch slots and the RVEs they hold
+    std::vector<ServeSlot> slots;
+    std::vector<uint8_t> in_flight;
+    std::vector<int32_t> class_of_fp64, class_of_mixed;  // RVE -> class index
 
     DevMesh mesh() const {
         DevMesh m;
@@ -179,6 +208,22 @@ struct fe2_batch {
         h_iters = nullptr;
         if (h_queue) cudaFreeHost(h_queue);
         h_queue = nullptr;
+        for (auto &sl : slots) {
+            if (sl.stream) cudaStreamDestroy(sl.stream);
+            if (sl.done) cudaEventDestroy(sl.done);
+            if (sl.d_ids) cudaFree(sl.d_ids);
+            if (sl.d_cnt) cudaFree(sl.d_cnt);
+            if (sl.d_F) cudaFree(sl.d_F);
+            if (sl.d_out) cudaFree(sl.d_out);
+            if (sl.d_it) cudaFree(sl.d_it);
+            if (sl.d_st) cudaFree(sl.d_st);
+            if (sl.h_ids) cudaFreeHost(sl.h_ids);
+            if (sl.h_F) cudaFreeHost(sl.h_F);
+            if (sl.h_out) cudaFreeHost(sl.h_out);
+            if (sl.h_it) cudaFreeHost(sl.h_it);
+            if (sl.h_st) cudaFreeHost(sl.h_st);
+        }
+        slots.clear();
         for (auto s : side) cudaStreamDestroy(s);
         for (auto e : ev) cudaEventDestroy(e);
         for (auto e : tev) cudaEventDestroy(e);
@@ -592,6 +637,32 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         A(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
         if (rc == FE2_OK) b->side.push_back(s);
     }
+    if (rc == FE2_OK) {
+        b->class_of_fp64.assign(n_rve, 0);
+        b->class_of_mixed.assign(n_rve, 0);
+        for (size_t k = 0; k < b->classes_fp64.size(); ++k)
+            for (int32_t p : b->classes_fp64[k].rves) b->class_of_fp64[p] = (int32_t)k;
+        for (size_t k = 0; k < b->classes_mixed.size(); ++k)
+            for (int32_t p : b->classes_mixed[k].rves) b->class_of_mixed[p] = (int32_t)k;
+        b->in_flight.assign(n_rve, 0);
+        b->slots.resize(kServeSlots);
+        for (auto &sl : b->slots) {
+            A(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "slot stream");
+            A(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "slot event");
+            A(cudaMalloc(&sl.d_ids, sizeof(int32_t) * 2 * n_rve), "slot ids");
+            A(cudaMalloc(&sl.d_cnt, sizeof(int32_t) * 32), "slot counters");
+            A(cudaMalloc(&sl.d_F, sizeof(double) * 9 * n_rve), "slot F");
+            A(cudaMalloc(&sl.d_out, sizeof(double) * 10 * n_rve), "slot out");
+            A(cudaMalloc(&sl.d_it, sizeof(int64_t) * n_rve), "slot iters");
+            A(cudaMalloc(&sl.d_st, sizeof(int32_t) * n_rve), "slot status");
+            A(cudaMallocHost(&sl.h_ids, sizeof(int32_t) * 2 * n_rve), "slot pinned ids");
+            A(cudaMallocHost(&sl.h_F, sizeof(double) * 9 * n_rve), "slot pinned F");
+            A(cudaMallocHost(&sl.h_out, sizeof(double) * 10 * n_rve), "slot pinned out");
+            A(cudaMallocHost(&sl.h_it, sizeof(int64_t) * n_rve), "slot pinned iters");
+            A(cudaMallocHost(&sl.h_st, sizeof(int32_t) * n_rve), "slot pinned status");
+            if (rc != FE2_OK) break;
+        }
+    }
     for (int k = 0; k < 8 && rc == FE2_OK; ++k) {
         cudaEvent_t e;
         A(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
@@ -660,15 +731,61 @@ fe2_status reorder_queues(fe2_batch *b) {
     return FE2_OK;
 }
 
-fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
+// Launch the solver kernels of one class on `s` for `nq` queued RVEs. Timing
+// events (tev) are recorded only when `timed` is non-null.
+fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, SolveParams P,
+                        const int32_t *queue, int nq, int32_t *counters, cudaStream_t s, int *timed,
+                        int *launches) {
     const bool fp64 = o.precision == FE2_PREC_FP64;
-    auto &classes = fp64 ? b->classes_fp64 : b->classes_mixed;
-    {
-        const fe2_status r = reorder_queues(b);
-        if (r != FE2_OK) return r;
+    const DevMesh M = b->mesh();
+    const DevState S = b->state();
+    const DevResults R = b->results();
+    P.queue = queue;
+    P.queue_len = nq;
+    P.counter = counters;
+    P.smem_positions = c.smem_positions;
+    if (fp64) {
+        const int block = o.block_threads ? o.block_threads : 512;
+        const size_t smem = c.smem_positions ? c.smem_bytes : 0;
+        const int per_sm = std::max(1, occupancy_dr_fp64(c.smem_positions, block, smem));
+        const int grid = std::max(1, std::min<int>(nq, per_sm * b->sm_count));
+        if (timed) {
+            if (*timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
+            CUDA_TRY(cudaEventRecord(b->tev[*timed], s));
+        }
+        const int e = launch_dr_fp64(M, S, R, P, grid, block, smem, s);
+        if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
+        if (timed) {
+            CUDA_TRY(cudaEventRecord(b->tev[*timed + 1], s));
+            *timed += 2;
+        }
+        ++*launches;
+    } else {
+        for (int lead = 1; lead >= 0; --lead) {
+            const int block = mixed_block(c, o.block_threads, lead != 0);
+            const size_t smem = lead ? kLeadNodeBytes * c.part_max : c.smem_bytes;
+            const int resident = occupancy_dr_mixed(lead, c.parts, block, smem);
+            if (resident < 1)
+                return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
+                                           std::to_string(smem) + " B shared memory fits");
+            if (timed) {
+                if (*timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
+                CUDA_TRY(cudaEventRecord(b->tev[*timed], s));
+            }
+            const int e = launch_dr_mixed(M, S, R, P, lead, std::min(nq, resident), c.parts, block, smem, s);
+            if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
+            if (timed) {
+                CUDA_TRY(cudaEventRecord(b->tev[*timed + 1], s));
+                *timed += 2;
+            }
+            ++*launches;
+        }
     }
-    CUDA_TRY(cudaMemsetAsync(b->d_counters.p, 0, sizeof(int32_t) * 32, st));
-    SolveParams P;
+    return FE2_OK;
+}
+
+SolveParams make_params(fe2_batch *b, const fe2_opts &o) {
+    SolveParams P = {};
     P.F = b->d_F.p;
     P.tol = o.tol;
     P.max_iter = o.max_iter;
@@ -678,9 +795,18 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
     P.lead_iters = o.lead_iters;
     P.lead_tol = o.lead_tol;
     P.rebase_every = o.rebase_every;
-    const DevMesh M = b->mesh();
-    const DevState S = b->state();
-    const DevResults R = b->results();
+    return P;
+}
+
+fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
+    const bool fp64 = o.precision == FE2_PREC_FP64;
+    auto &classes = fp64 ? b->classes_fp64 : b->classes_mixed;
+    {
+        const fe2_status r = reorder_queues(b);
+        if (r != FE2_OK) return r;
+    }
+    CUDA_TRY(cudaMemsetAsync(b->d_counters.p, 0, sizeof(int32_t) * 32, st));
+    const SolveParams P = make_params(b, o);
     // fork: every class runs on its own stream, concurrently
     CUDA_TRY(cudaEventRecord(b->ev[0], st));
     int launches = 0, timed = 0;
@@ -688,42 +814,9 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
         const SizeClass &c = classes[k];
         cudaStream_t s = b->side[k];
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev[0], 0));
-        P.queue = b->d_queue.p + (fp64 ? 0 : b->n_rve) + c.queue_off;
-        P.queue_len = (int32_t)c.rves.size();
-        P.counter = b->d_counters.p + 2 * k;
-        P.smem_positions = c.smem_positions;
-        const int nq = (int)c.rves.size();
-        if (fp64) {
-            const int block = o.block_threads ? o.block_threads : 512;
-            const size_t smem = c.smem_positions ? c.smem_bytes : 0;
-            const int per_sm = std::max(1, occupancy_dr_fp64(c.smem_positions, block, smem));
-            const int grid = std::max(1, std::min<int>(nq, per_sm * b->sm_count));
-            if (timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
-            CUDA_TRY(cudaEventRecord(b->tev[timed], s));
-            const int e = launch_dr_fp64(M, S, R, P, grid, block, smem, s);
-            if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
-            CUDA_TRY(cudaEventRecord(b->tev[timed + 1], s));
-            timed += 2;
-            ++launches;
-        } else {
-            for (int lead = 1; lead >= 0; --lead) {
-                const int block = mixed_block(c, o.block_threads, lead != 0);
-                const size_t smem = lead ? kLeadNodeBytes * c.part_max : c.smem_bytes;
-                const int resident = occupancy_dr_mixed(lead, c.parts, block, smem);
-                if (resident < 1)
-                    return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
-                                               std::to_string(smem) + " B shared memory fits");
-                if (timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
-                CUDA_TRY(cudaEventRecord(b->tev[timed], s));
-                const int e = launch_dr_mixed(M, S, R, P, lead, std::min(nq, resident), c.parts, block,
-                                              smem, s);
-                if (e != 0)
-                    return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
-                CUDA_TRY(cudaEventRecord(b->tev[timed + 1], s));
-                timed += 2;
-                ++launches;
-            }
-        }
+        const fe2_status r = launch_class(b, o, c, P, b->d_queue.p + (fp64 ? 0 : b->n_rve) + c.queue_off,
+                                          (int)c.rves.size(), b->d_counters.p + 2 * k, s, &timed, &launches);
+        if (r != FE2_OK) return r;
         CUDA_TRY(cudaEventRecord(b->ev[1 + k], s));
         CUDA_TRY(cudaStreamWaitEvent(st, b->ev[1 + k], 0));
     }
@@ -908,5 +1001,223 @@ extern "C" fe2_status fe2_batch_solve_naive(fe2_batch *b, const double *F, const
     b->last_timed = 0;
     b->last_stream = st;
     b->solved = true;
+    return FE2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: continuous micro-batching. A submission stages the deformation
+// gradients of a set of RVEs, launches the solver for just those RVEs on a
+// stream of its own (so in-flight submissions overlap on the device) and
+// queues the copy of their results; poll hands back finished submissions.
+// Every RVE keeps its state on the device between submissions, which is what
+// FE2_INIT_WARM restarts from.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_scatter_F(int n, const int32_t *ids, const double *Fs, double *F) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 9 * n) return;
+    F[9 * (int64_t)ids[t / 9] + t % 9] = Fs[t];
+}
+
+__global__ void k_gather_results(int n, const int32_t *ids, const double *sigma, const double *rel,
+                                 const int64_t *iters, const int32_t *status, double *out,
+                                 int64_t *it_out, int32_t *st_out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t p = ids[t];
+    for (int k = 0; k < 9; ++k) out[10 * (int64_t)t + k] = sigma[9 * p + k];
+    out[10 * (int64_t)t + 9] = rel[p];
+    it_out[t] = iters[p];
+    st_out[t] = status[p];
+}
+
+double working_bytes(const fe2_batch *b, int32_t p) {
+    // device state a solve keeps busy: mixed staging + per-node solver arrays
+    return 200.0 * (double)b->rve[p].n_nodes;
+}
+
+}  // namespace
+
+extern "C" fe2_status fe2_batch_submit(fe2_batch *b, int32_t n, const int32_t *rve_ids,
+                                       const double *F, const fe2_opts *opts, int32_t *ticket) {
+    if (!b || !rve_ids || !F || n < 1) return fail(FE2_EINVAL, "NULL argument or n < 1");
+    if (n > b->n_rve) return fail(FE2_EINVAL, "more RVEs than the batch holds");
+    fe2_opts o;
+    if (opts) o = *opts; else fe2_opts_default(&o);
+    fe2_status st = check_opts(o);
+    if (st != FE2_OK) return st;
+    for (int32_t k = 0; k < n; ++k) {
+        if (rve_ids[k] < 0 || rve_ids[k] >= b->n_rve) return fail(FE2_EINVAL, "RVE id out of range");
+        if (b->in_flight[rve_ids[k]]) return fail(FE2_EINVAL, "RVE " + std::to_string(rve_ids[k]) + " is already in flight");
+    }
+    int slot = -1;
+    for (size_t k = 0; k < b->slots.size(); ++k)
+        if (!b->slots[k].busy) { slot = (int)k; break; }
+    if (slot < 0) return fail(FE2_EBUSY, "every serving slot is in flight");
+    ServeSlot &sl = b->slots[slot];
+    const bool fp64 = o.precision == FE2_PREC_FP64;
+    auto &classes = fp64 ? b->classes_fp64 : b->classes_mixed;
+    auto &class_of = fp64 ? b->class_of_fp64 : b->class_of_mixed;
+    // staged ids, then the ids again grouped by class (largest first)
+    std::vector<std::vector<int32_t>> per(classes.size());
+    for (int32_t k = 0; k < n; ++k) {
+        // mark duplicates within one submission as errors
+        for (int32_t j = 0; j < k; ++j)
+            if (rve_ids[j] == rve_ids[k]) return fail(FE2_EINVAL, "RVE id repeated in one submission");
+        per[class_of[rve_ids[k]]].push_back(rve_ids[k]);
+        sl.h_ids[k] = rve_ids[k];
+    }
+    int32_t off = n;
+    std::vector<std::pair<int, int32_t>> starts;
+    for (size_t c = 0; c < per.size(); ++c) {
+        std::stable_sort(per[c].begin(), per[c].end(), [&](int32_t x, int32_t y) {
+            return b->rve[x].n_free > b->rve[y].n_free;
+        });
+        starts.emplace_back((int)c, off);
+        for (int32_t id : per[c]) sl.h_ids[off++] = id;
+    }
+    std::memcpy(sl.h_F, F, sizeof(double) * 9 * n);
+    cudaStream_t s = sl.stream;
+    CUDA_TRY(cudaMemcpyAsync(sl.d_ids, sl.h_ids, sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(sl.d_F, sl.h_F, sizeof(double) * 9 * n, cudaMemcpyHostToDevice, s));
+    k_scatter_F<<<(9 * n + 255) / 256, 256, 0, s>>>(n, sl.d_ids, sl.d_F, b->d_F.p);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemsetAsync(sl.d_cnt, 0, sizeof(int32_t) * 32, s));
+    const SolveParams P = make_params(b, o);
+    int launches = 0;
+    for (auto &[c, q0] : starts) {
+        if (per[c].empty()) continue;
+        const fe2_status r = launch_class(b, o, classes[c], P, sl.d_ids + q0, (int)per[c].size(),
+                                          sl.d_cnt + 2 * c, s, nullptr, &launches);
+        if (r != FE2_OK) return r;
+    }
+    k_gather_results<<<(n + 127) / 128, 128, 0, s>>>(n, sl.d_ids, b->d_sigma.p, b->d_rel.p, b->d_iters.p,
+                                                     b->d_status.p, sl.d_out, sl.d_it, sl.d_st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(sl.h_out, sl.d_out, sizeof(double) * 10 * n, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(sl.h_it, sl.d_it, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(sl.h_st, sl.d_st, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaEventRecord(sl.done, s));
+    sl.n = n;
+    sl.busy = true;
+    sl.bytes = 0.0;
+    for (int32_t k = 0; k < n; ++k) {
+        b->in_flight[rve_ids[k]] = 1;
+        sl.bytes += working_bytes(b, rve_ids[k]);
+    }
+    b->solved = true;
+    b->last_stream = s;
+    if (ticket) *ticket = slot;
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_poll(fe2_batch *b, int32_t max, int32_t *ids, double *sigma,
+                                     int64_t *iters, double *rel_res, int32_t *status, int32_t *n_out) {
+    if (!b || !n_out) return fail(FE2_EINVAL, "NULL batch or n_out");
+    *n_out = 0;
+    for (auto &sl : b->slots) {
+        if (!sl.busy) continue;
+        const cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return fail(FE2_ECUDA, std::string("serving slot: ") + cudaGetErrorString(q));
+        if (*n_out + sl.n > max) break;  // no room: leave it for the next poll
+        for (int k = 0; k < sl.n; ++k) {
+            const int o = *n_out + k;
+            if (ids) ids[o] = sl.h_ids[k];
+            if (sigma) std::memcpy(sigma + 9 * (int64_t)o, sl.h_out + 10 * (int64_t)k, sizeof(double) * 9);
+            if (rel_res) rel_res[o] = sl.h_out[10 * (int64_t)k + 9];
+            if (iters) iters[o] = sl.h_it[k];
+            if (status) status[o] = sl.h_st[k];
+            b->in_flight[sl.h_ids[k]] = 0;
+        }
+        *n_out += sl.n;
+        sl.busy = false;
+        sl.n = 0;
+    }
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_serve(fe2_batch *b, int32_t n_req, const int32_t *rve, const double *t_arrive,
+                                const double *F, const fe2_opts *opts_first, const fe2_opts *opts_next,
+                                int32_t max_batch, double max_inflight_bytes, double *t_done,
+                                int64_t *iters, int32_t *status, double *sigma) {
+    if (!b || n_req < 0 || (n_req > 0 && (!rve || !t_arrive || !F || !t_done)))
+        return fail(FE2_EINVAL, "NULL argument");
+    if (max_batch < 1) max_batch = b->n_rve;
+    for (int32_t r = 0; r < n_req; ++r) {
+        if (rve[r] < 0 || rve[r] >= b->n_rve) return fail(FE2_EINVAL, "request RVE id out of range");
+        if (r > 0 && t_arrive[r] < t_arrive[r - 1]) return fail(FE2_EINVAL, "arrival times must not decrease");
+    }
+    for (auto &sl : b->slots)
+        if (sl.busy) return fail(FE2_ESTATE, "serving slots are busy; poll them first");
+    // per RVE: its requests in arrival order; a request becomes eligible once it
+    // has arrived and the previous request of its RVE has completed
+    std::vector<std::vector<int32_t>> chain(b->n_rve);
+    for (int32_t r = 0; r < n_req; ++r) chain[rve[r]].push_back(r);
+    std::vector<int32_t> next(b->n_rve, 0);           // index into chain of the next request
+    std::vector<int32_t> running(b->n_rve, -1);       // request in flight per RVE
+    std::vector<uint8_t> seen(b->n_rve, 0);           // RVE already solved once (warm start)
+    std::vector<int32_t> ids(b->n_rve), done_ids(b->n_rve);
+    std::vector<double> Fs(9 * (size_t)b->n_rve), sig(9 * (size_t)b->n_rve), rr(b->n_rve);
+    std::vector<int64_t> its(b->n_rve);
+    std::vector<int32_t> sts(b->n_rve);
+    fe2_opts of, on;
+    if (opts_first) of = *opts_first; else fe2_opts_default(&of);
+    if (opts_next) on = *opts_next; else { on = of; on.init = FE2_INIT_WARM; }
+    int32_t completed = 0;
+    double inflight = 0.0;
+    const auto t0 = std::chrono::steady_clock::now();
+    auto now = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+    while (completed < n_req) {
+        // completions
+        int32_t got = 0;
+        fe2_status st = fe2_batch_poll(b, b->n_rve, done_ids.data(), sig.data(), its.data(), rr.data(),
+                                       sts.data(), &got);
+        if (st != FE2_OK) return st;
+        const double tn = now();
+        for (int32_t k = 0; k < got; ++k) {
+            const int32_t p = done_ids[k], r = running[p];
+            t_done[r] = tn;
+            if (iters) iters[r] = its[k];
+            if (status) status[r] = sts[k];
+            if (sigma) std::memcpy(sigma + 9 * (int64_t)r, sig.data() + 9 * (size_t)k, sizeof(double) * 9);
+            running[p] = -1;
+            inflight -= working_bytes(b, p);
+            ++completed;
+        }
+        // admission: arrived, eligible, within slots and the working-set budget
+        for (int pass = 0; pass < 2; ++pass) {  // first solves, then warm restarts
+            const bool warm = pass == 1;
+            int32_t n = 0;
+            for (int32_t p = 0; p < b->n_rve && n < max_batch; ++p) {
+                if (running[p] >= 0 || next[p] >= (int32_t)chain[p].size()) continue;
+                if ((seen[p] != 0) != warm) continue;
+                const int32_t r = chain[p][next[p]];
+                if (t_arrive[r] > tn) continue;
+                const double wb = working_bytes(b, p);
+                if (max_inflight_bytes > 0.0 && inflight + wb > max_inflight_bytes && inflight > 0.0) continue;
+                ids[n] = p;
+                std::memcpy(Fs.data() + 9 * (size_t)n, F + 9 * (int64_t)r, sizeof(double) * 9);
+                inflight += wb;
+                ++n;
+            }
+            if (n == 0) continue;
+            int32_t ticket = -1;
+            st = fe2_batch_submit(b, n, ids.data(), Fs.data(), warm ? &on : &of, &ticket);
+            if (st == FE2_EBUSY) {  // no free slot: undo and retry after the next poll
+                for (int32_t k = 0; k < n; ++k) inflight -= working_bytes(b, ids[k]);
+                break;
+            }
+            if (st != FE2_OK) return st;
+            for (int32_t k = 0; k < n; ++k) {
+                const int32_t p = ids[k];
+                running[p] = chain[p][next[p]];
+                ++next[p];
+                seen[p] = 1;
+            }
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
     return FE2_OK;
 }
