@@ -333,6 +333,55 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_serving(args):
+    """Serving scenario: Gauss points of a synthetic macroscale mesh emit one
+    RVE request per macro step; arrivals are Poisson; F grows by 0.5 % stretch
+    per step; each RVE restarts warm from its previous step, on the device.
+    Reports throughput and p50/p99 request latency (arrival to completion)."""
+    import torch
+    import paper_2305_07030_gb300 as fe2
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    n_pts, n_steps = args.serve_points, args.serve_steps
+    sizes, S, arrivals = ri.serving_requests(n_pts, n_steps, args.serve_lo, args.serve_hi,
+                                             rate=args.serve_rate)
+    nets = []
+    for g in range(n_pts):
+        rng = np.random.Generator(np.random.PCG64((ri.SEED_BASE + 5) * 1000 + g))
+        nets.append(ri.random_network(int(sizes[g]), rng))
+    damping = np.array([ri.default_damping(int(n)) for n in sizes])
+    rve, t_arr, F = [], [], []
+    for k in range(n_steps):
+        for g in range(n_pts):
+            rve.append(g)
+            t_arr.append(arrivals[k, g])
+            F.append(ri.serving_F(S[g], k))
+    order = np.argsort(np.array(t_arr), kind="stable")
+    rve = np.array(rve, np.int32)[order]
+    t_arr = np.array(t_arr)[order]
+    t_arr -= t_arr[0]
+    F = np.array(F)[order]
+    with fe2.Batch(nets, damping=damping) as b:
+        t0 = time.perf_counter()
+        out = b.serve(rve, t_arr, F, max_batch=args.serve_batch)
+        wall = time.perf_counter() - t0
+    lat = out["t_done"] - t_arr
+    return {"metric": "serving p99 latency", "value": float(np.percentile(lat, 99)), "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "dtype": "f32+f64",
+            "config": {"workload": f"{n_pts} Gauss points x {n_steps} macro steps, RVE nodes "
+                                   f"log-U({args.serve_lo},{args.serve_hi}), Poisson arrivals "
+                                   f"{args.serve_rate}/s, F=diag(1+0.005k,1,1)(I+0.02 S), warm "
+                                   f"restarts, micro-batches <= {args.serve_batch}"},
+            "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)),
+            "latency_max_s": float(lat.max()),
+            "requests": int(len(rve)), "wall_s": wall,
+            "throughput_req_per_s": len(rve) / wall,
+            "iters_first_step_mean": float(out["iters"][:n_pts].mean()),
+            "iters_mean": float(out["iters"].mean()),
+            "status_ok": int((out["status"] == 0).sum())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,9 +397,20 @@ def main():
     ap.add_argument("--max-iter", type=int, default=10_000_000)
     ap.add_argument("--lead-iters", type=int, default=-1)
     ap.add_argument("--block", type=int, default=0, help="threads per CTA (0 = library default)")
+    ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
+    ap.add_argument("--serve-points", type=int, default=128)
+    ap.add_argument("--serve-steps", type=int, default=3)
+    ap.add_argument("--serve-lo", type=int, default=1000)
+    ap.add_argument("--serve-hi", type=int, default=8000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-batch", type=int, default=32)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.serve:
+        if rank == 0:
+            print(json.dumps(run_serving(args)))
+        return
     if args.impl == "reference":
         if rank != 0:
             return

@@ -81,8 +81,6 @@ def test_request_loop_with_warm_restarts_matches_replay():
     assert np.all(out["t_done"] >= t_arr)
     # replay: each RVE's chain alone, in order, on a fresh batch
     with Batch(w.nets, damping=w.damping) as b2:
-        for r, (p, k) in enumerate(reqs):
-            pass
         for p in range(w.n_rve):
             for r in [i for i, (q, _) in enumerate(reqs) if q == p]:
                 init = "affine" if reqs[r][1] == 0 else "warm"
