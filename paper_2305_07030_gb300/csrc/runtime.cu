@@ -89,7 +89,7 @@ struct ServeSlot {
     double bytes = 0.0;         // working-set bytes it holds (admission)
 };
 
-constexpr int kServeSlots = 8;  // concurrent micro-batches of the serving interface
+constexpr int kServeSlots = 32;  // concurrent micro-batches of the serving interface
 
 int env_int(const char *name, int dflt) {
     const char *v = std::getenv(name);
