@@ -187,7 +187,7 @@ fe2_status fe2_batch_parts(const fe2_batch *b, int32_t *parts);
  * doubles row-major) and launch the solver for just those RVEs on a stream of
  * its own, returning at once. Submissions in flight overlap on the device. An
  * RVE keeps its state on the device, so opts->init = FE2_INIT_WARM restarts
- * from its last result. FE2_EBUSY when all 32 slots are in flight; FE2_EINVAL
+ * from its last result. FE2_EBUSY when all 8 slots are in flight; FE2_EINVAL
  * if an id is out of range, repeated, or already in flight.
  *
  * fe2_batch_poll: hand back every finished submission that fits in `max`

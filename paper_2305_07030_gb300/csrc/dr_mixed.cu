@@ -131,19 +131,33 @@ __device__ __forceinline__ void publish(MixedShared &sh, const Part &pt, float v
     }
 }
 
+// Combine double-float partial sums over groups of L consecutive lanes (every
+// lane of the warp must call this).
+__device__ __forceinline__ void df_group_sum(df &g0, df &g1, df &g2, int L) {
+    for (int o = 1; o < L; o <<= 1) {
+        const df a0 = {__shfl_xor_sync(0xffffffffu, g0.hi, o), __shfl_xor_sync(0xffffffffu, g0.lo, o)};
+        const df a1 = {__shfl_xor_sync(0xffffffffu, g1.hi, o), __shfl_xor_sync(0xffffffffu, g1.lo, o)};
+        const df a2 = {__shfl_xor_sync(0xffffffffu, g2.hi, o), __shfl_xor_sync(0xffffffffu, g2.lo, o)};
+        g0 = df_add(g0, a0);
+        g1 = df_add(g1, a1);
+        g2 = df_add(g2, a2);
+    }
+}
+
 // Double-float internal force on own node k (Algorithm 1, getInternalForces)
 // in displacement form; the node's and its neighbours' displacements are
 // staged as (hi, lo) in (Pl, Ql) and the other CTAs' copies (Q buffer qbuf).
 __device__ __forceinline__ void gather_df(const DevMesh &M, const RveDesc &R, const int32_t *rowptr,
                                           const MixedShared &sh, const Part &pt, int k,
                                           const float4 *Pl, const float4 *Ql, int qbuf, df &g0,
-                                          df &g1, df &g2) {
+                                          df &g1, df &g2, int sub = 0, int L = 1) {
     const int gi = pt.gidx(k);
     const float4 pi = Pl[k], qi = Ql[k];
     const df ui0 = {pi.x, qi.x}, ui1 = {pi.y, qi.y}, ui2 = {pi.z, qi.z};
     g0 = df_from(0.f); g1 = df_from(0.f); g2 = df_from(0.f);
     const int beg = rowptr[gi], end = rowptr[gi + 1];
-    for (int e = beg; e < end; ++e) {
+    // lane `sub` of L takes edges sub, sub+L, ... (the caller combines the lanes)
+    for (int e = beg + sub; e < end; e += L) {
         const int64_t kk = R.csr0 + e;
         const int cp = M.col_part[kk];
         const int r = cp >> 16, loc = cp & 0xffff;
@@ -281,8 +295,14 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
     int64_t it = 0;
     int status = RVE_PENDING;
     df r2 = df_from(0.f), k2 = df_from(0.f);
+    // L lanes share a node's edges; lane 0 of group k owns node k's state in
+    // every phase, so consecutive phases need no barrier between them.
+    int L = 1;
+    while (L < 4 && (int)blockDim.x >= 2 * L * R.part_free_max) L *= 2;
+    const int sub = threadIdx.x & (L - 1), grp = threadIdx.x / L, ngrp = blockDim.x / L;
     for (;;) {
-        for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+        for (int k = grp; k < pt.nfr; k += ngrp) {
+            if (sub != 0) continue;
             const int i = pt.f0 + k;
             df u[3];
             for (int c = 0; c < 3; ++c) {
@@ -298,10 +318,14 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         }
         cl.sync();
         float rs = 0.f, kes = 0.f;
-        for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+        for (int kb = 0; kb < pt.nfr; kb += ngrp) {
+            const int k = kb + grp;
+            const bool valid = k < pt.nfr;
+            df g[3] = {df_from(0.f), df_from(0.f), df_from(0.f)};
+            if (valid) gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g[0], g[1], g[2], sub, L);
+            df_group_sum(g[0], g[1], g[2], L);
+            if (!valid || sub != 0) continue;
             const int i = pt.f0 + k;
-            df g[3];
-            gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g[0], g[1], g[2]);
             const df im = {imh[i], iml[i]};
             float vv = 0.f;
             for (int c = 0; c < 3; ++c) {
@@ -653,7 +677,7 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) dr_mixed_lead_kernel(DevMesh M, DevState S, DevResults O,
+__global__ void __launch_bounds__(512) dr_mixed_lead_kernel(DevMesh M, DevState S, DevResults O,
                                                             SolveParams P, int part_cap) {
     extern __shared__ __align__(16) float4 dsm[];
     __shared__ MixedShared sh;

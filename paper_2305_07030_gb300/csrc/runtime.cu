@@ -89,7 +89,7 @@ struct ServeSlot {
     double bytes = 0.0;         // working-set bytes it holds (admission)
 };
 
-constexpr int kServeSlots = 32;  // concurrent micro-batches of the serving interface
+constexpr int kServeSlots = 8;  // concurrent micro-batches of the serving interface
 
 int env_int(const char *name, int dflt) {
     const char *v = std::getenv(name);
@@ -697,13 +697,13 @@ fe2_status check_opts(const fe2_opts &o) {
     return FE2_OK;
 }
 
-// Threads per CTA of the mixed solver's FP32 kernel (the lead kernel is
-// bounded to 256). A fixed default keeps every RVE's result independent of
-// which other RVEs share its launch (partial sums follow the thread mapping).
+// Threads per CTA of the mixed solver's kernels. A fixed default keeps every
+// RVE's result independent of which other RVEs share its launch (partial sums
+// follow the thread mapping).
 int mixed_block(const SizeClass &c, int requested, bool lead) {
     (void)c;
-    const int b = requested ? requested : (lead ? 256 : 512);
-    return lead ? std::min(b, 256) : b;
+    (void)lead;
+    return requested ? requested : 512;
 }
 
 // Longest-processing-time order from measured cost: once a solve has
