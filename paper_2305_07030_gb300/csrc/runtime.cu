@@ -697,13 +697,15 @@ fe2_status check_opts(const fe2_opts &o) {
     return FE2_OK;
 }
 
-// Threads per CTA of the mixed solver's kernels. A fixed default keeps every
-// RVE's result independent of which other RVEs share its launch (partial sums
-// follow the thread mapping).
+// Threads per CTA of the mixed solver's kernels: 256 for the double-float lead
+// (two CTAs per SM keep more clusters resident), 512 for the FP32 kernel (more
+// warps to hide its latency chain). A fixed default keeps every RVE's result
+// independent of which other RVEs share its launch (partial sums follow the
+// thread mapping).
 int mixed_block(const SizeClass &c, int requested, bool lead) {
     (void)c;
-    (void)lead;
-    return requested ? requested : 512;
+    if (requested) return lead ? std::min(requested, 256) : requested;
+    return lead ? 256 : 512;
 }
 
 // Longest-processing-time order from measured cost: once a solve has
