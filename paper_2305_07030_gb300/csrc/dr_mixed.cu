@@ -52,6 +52,7 @@ constexpr int kBufs = 3;       // rotating increment / partial buffers
 // FP32 kernel shared memory per staged node: reference position, three
 // increment buffers (float4 each), velocity + a.x (float4), a.yz (float2).
 constexpr size_t kFp32NodeBytes = (1 + kBufs + 1) * sizeof(float4) + sizeof(float2);
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 struct MixedShared {
     float red[kBufs][kMaxParts * kMaxWarps];  // per-warp residual partials of every CTA,
@@ -387,9 +388,18 @@ __device__ __forceinline__ void edge_increment(const float4 &pi, const float4 &q
 // ---------------------------------------------------------------------------
 // FP32 kernel: increment iterations, reference refreshes, final state, stress
 // ---------------------------------------------------------------------------
+// Shared-memory staging of one part's CSR rows for the FP32 kernel.
+struct Staged {
+    float4 *SG;  // per own free node: (g_ref, 1/m)
+    int *SR;     // per own free node + 1: row offsets into SC / SE
+    int *SC;     // neighbour as (part << 16 | index in part)
+    float2 *SE;  // (EA, 1/L)
+};
+
+template <bool STAGE>
 __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
                          const DevResults &O, const SolveParams &P, int p, float4 *Pl,
-                         float4 *const *Qb, float4 *SV, float2 *SA, int &rb) {
+                         float4 *const *Qb, float4 *SV, float2 *SA, const Staged &st, int &rb) {
     const RveDesc R = M.rve[p];
     const Part pt = make_part(M, R, p, (int)cl.block_rank(), (int)cl.num_blocks());
     const int n = R.n_nodes, m = pt.m();
@@ -438,6 +448,18 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             if (k < pt.nfr) {
                 SV[k] = make_float4(vh[i], vh[n + i], vh[2 * n + i], ah[i]);
                 SA[k] = make_float2(ah[n + i], ah[2 * n + i]);
+                if (STAGE) {
+                    st.SG[k] = make_float4(fg[i], fg[n + i], fg[2 * n + i], imh[i]);
+                    st.SR[k] = rowptr[i] - rowptr[pt.f0];
+                }
+            }
+        }
+        if (STAGE) {
+            const int e0 = rowptr[pt.f0], ne = rowptr[pt.f0 + pt.nfr] - e0;
+            if (threadIdx.x == 0) st.SR[pt.nfr] = ne;
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                st.SC[e] = M.col_part[R.csr0 + e0 + e];
+                st.SE[e] = M.eaf[R.csr0 + e0 + e];
             }
         }
         cl.sync();
@@ -521,6 +543,7 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     df g[3];
                     gather_df(M, R, rowptr, sh, pt, k, Pl, cur, b, g[0], g[1], g[2]);
                     fg[i] = g[0].hi; fg[n + i] = g[1].hi; fg[2 * n + i] = g[2].hi;
+                    if (STAGE) st.SG[k] = make_float4(g[0].hi, g[1].hi, g[2].hi, imh[i]);
                 }
                 cl.sync();
                 // back to FP32 reference positions and zero increments
@@ -559,11 +582,16 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     if (valid) {
                         const int i = pt.f0 + k;
                         const float4 pi = Pl[k], qi = cur[k];
-                        const int end = rowptr[i + 1];
-                        int e = rowptr[i] + sub;
+                        // rows from shared memory (STAGE) or from global memory
+                        const int32_t *cpp = STAGE ? st.SC : colp;
+                        const float2 *epp = STAGE ? st.SE : eafp;
+                        const int end = STAGE ? st.SR[k + 1] : rowptr[i + 1];
+                        int e = (STAGE ? st.SR[k] : rowptr[i]) + sub;
                         for (; e + L < end; e += 2 * L) {
-                            const int ca = __ldg(colp + e), cb = __ldg(colp + e + L);
-                            const float2 ea = __ldg(eafp + e), eb = __ldg(eafp + e + L);
+                            const int ca = STAGE ? cpp[e] : __ldg(cpp + e);
+                            const int cb = STAGE ? cpp[e + L] : __ldg(cpp + e + L);
+                            const float2 ea = STAGE ? epp[e] : __ldg(epp + e);
+                            const float2 eb = STAGE ? epp[e + L] : __ldg(epp + e + L);
                             const int ra = ca >> 16, la = ca & 0xffff, rb2 = cb >> 16, lb = cb & 0xffff;
                             const float4 pa = ra == pt.me ? Pl[la] : sh.P[ra][la];
                             const float4 qa = ra == pt.me ? cur[la] : sh.Q[b][ra][la];
@@ -573,8 +601,8 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                             edge_increment(pi, qi, pb, qb, eb, g0, g1, g2);
                         }
                         if (e < end) {
-                            const int ca = __ldg(colp + e);
-                            const float2 ea = __ldg(eafp + e);
+                            const int ca = STAGE ? cpp[e] : __ldg(cpp + e);
+                            const float2 ea = STAGE ? epp[e] : __ldg(epp + e);
                             const int ra = ca >> 16, la = ca & 0xffff;
                             const float4 pa = ra == pt.me ? Pl[la] : sh.P[ra][la];
                             const float4 qa = ra == pt.me ? cur[la] : sh.Q[b][ra][la];
@@ -588,8 +616,15 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     }
                     if (valid && sub == 0) {
                         const int i = pt.f0 + k;
-                        g0 += fg[i]; g1 += fg[n + i]; g2 += fg[2 * n + i];
-                        const float im = imh[i];
+                        float im;
+                        if (STAGE) {
+                            const float4 gr = st.SG[k];
+                            g0 += gr.x; g1 += gr.y; g2 += gr.z;
+                            im = gr.w;
+                        } else {
+                            g0 += fg[i]; g1 += fg[n + i]; g2 += fg[2 * n + i];
+                            im = imh[i];
+                        }
                         const float4 va = SV[k];
                         float w0 = va.x, w1 = va.y, w2 = va.z;
                         const float a0 = g0 * im - cf * w0;
@@ -693,8 +728,10 @@ __global__ void __launch_bounds__(512) dr_mixed_lead_kernel(DevMesh M, DevState 
     }
 }
 
+template <bool STAGE>
 __global__ void __launch_bounds__(512, 1) dr_mixed_fp32_kernel(DevMesh M, DevState S, DevResults O,
-                                                               SolveParams P, int part_cap) {
+                                                               SolveParams P, int part_cap,
+                                                               int free_cap, int edge_cap) {
     extern __shared__ __align__(16) float4 dsm[];
     __shared__ MixedShared sh;
     cg::cluster_group cl = cg::this_cluster();
@@ -702,12 +739,20 @@ __global__ void __launch_bounds__(512, 1) dr_mixed_fp32_kernel(DevMesh M, DevSta
     float4 *Qb[kBufs] = {dsm + part_cap, dsm + 2 * part_cap, dsm + 3 * part_cap};
     float4 *SV = dsm + 4 * part_cap;
     float2 *SA = reinterpret_cast<float2 *>(dsm + 5 * part_cap);
+    Staged st = {};
+    if (STAGE) {
+        char *base = reinterpret_cast<char *>(dsm) + align16(kFp32NodeBytes * part_cap);
+        st.SG = reinterpret_cast<float4 *>(base);
+        st.SE = reinterpret_cast<float2 *>(base + 16 * (size_t)free_cap);
+        st.SC = reinterpret_cast<int *>(base + 16 * (size_t)free_cap + 8 * (size_t)edge_cap);
+        st.SR = reinterpret_cast<int *>(base + 16 * (size_t)free_cap + 12 * (size_t)edge_cap);
+    }
     map_remote(cl, sh, Pl, Qb, (int)cl.num_blocks());
     int rb = 0;
     for (;;) {
         const int item = next_item(cl, sh, P.counter + 1);
         if (item >= P.queue_len) return;
-        fp32_rve(cl, sh, M, S, O, P, P.queue[item], Pl, Qb, SV, SA, rb);
+        fp32_rve<STAGE>(cl, sh, M, S, O, P, P.queue[item], Pl, Qb, SV, SA, st, rb);
     }
 }
 
@@ -735,8 +780,16 @@ void prepare(K kernel, size_t smem) {
 }
 }  // namespace
 
+size_t mixed_fp32_smem(int part_cap, int free_cap, int edge_cap, size_t limit) {
+    const size_t plain = kFp32NodeBytes * (size_t)part_cap;
+    const size_t staged = align16(align16(plain) + 16 * (size_t)free_cap + 12 * (size_t)edge_cap +
+                                  4 * ((size_t)free_cap + 1));
+    return staged <= limit ? staged : plain;
+}
+
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
-                    int lead, int clusters, int parts, int block, size_t smem, void *stream) {
+                    int lead, int clusters, int parts, int block, size_t smem, int part_cap,
+                    int free_cap, int edge_cap, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = mixed_config(clusters, parts, block, smem, attr, st);
@@ -745,16 +798,23 @@ int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, co
         prepare(dr_mixed_lead_kernel, smem);
         e = cudaLaunchKernelEx(&cfg, dr_mixed_lead_kernel, m, s, r, p,
                                (int)(smem / (2 * sizeof(float4))));
+    } else if (smem > kFp32NodeBytes * (size_t)part_cap) {
+        prepare(dr_mixed_fp32_kernel<true>, smem);
+        e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel<true>, m, s, r, p, part_cap, free_cap,
+                               edge_cap);
     } else {
-        prepare(dr_mixed_fp32_kernel, smem);
-        e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel, m, s, r, p,
-                               (int)(smem / kFp32NodeBytes));
+        prepare(dr_mixed_fp32_kernel<false>, smem);
+        e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel<false>, m, s, r, p, part_cap, free_cap,
+                               edge_cap);
     }
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 
-int occupancy_dr_mixed(int lead, int parts, int block, size_t smem) {
+int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap, int free_cap,
+                       int edge_cap) {
+    (void)free_cap;
+    (void)edge_cap;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = mixed_config(parts * 64, parts, block, smem, attr, nullptr);
     int n = 0;
@@ -762,9 +822,12 @@ int occupancy_dr_mixed(int lead, int parts, int block, size_t smem) {
     if (lead) {
         prepare(dr_mixed_lead_kernel, smem);
         e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_lead_kernel, &cfg);
+    } else if (smem > kFp32NodeBytes * (size_t)part_cap) {
+        prepare(dr_mixed_fp32_kernel<true>, smem);
+        e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_fp32_kernel<true>, &cfg);
     } else {
-        prepare(dr_mixed_fp32_kernel, smem);
-        e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_fp32_kernel, &cfg);
+        prepare(dr_mixed_fp32_kernel<false>, smem);
+        e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_fp32_kernel<false>, &cfg);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

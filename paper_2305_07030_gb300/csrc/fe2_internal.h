@@ -39,6 +39,8 @@ struct RveDesc {
     double V0;        // reference volume
     int32_t part_max;       // largest part (nodes), sizes the shared memory
     int32_t part_free_max;  // most free nodes in one part
+    int32_t part_edge_max;  // most CSR entries of one part's free nodes
+    int32_t pad;
 };
 
 // Read-only, create-time arrays.
@@ -116,10 +118,14 @@ int launch_dr_fp64(const DevMesh &m, const DevState &s, const DevResults &r,
 // the FP32 phase (lead = 0).
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r,
                     const SolveParams &p, int lead, int clusters, int parts, int block,
-                    size_t smem, void *stream);
+                    size_t smem, int part_cap, int free_cap, int edge_cap, void *stream);
+// Dynamic shared memory of the FP32 kernel for a class: the staged node state,
+// plus each part's CSR rows when they fit within `limit` bytes.
+size_t mixed_fp32_smem(int part_cap, int free_cap, int edge_cap, size_t limit);
 // Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.
 int occupancy_dr_fp64(int smem_positions, int block, size_t smem);
-int occupancy_dr_mixed(int lead, int parts, int block, size_t smem);
+int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap, int free_cap,
+                       int edge_cap);
 
 // Naive comparator: scratch sized for the largest RVE, and one RVE's solve.
 struct NaiveScratch {

@@ -64,6 +64,7 @@ struct SizeClass {
     size_t smem_bytes = 0;      // dynamic shared memory per CTA
     int part_max = 0;           // mixed: largest part (nodes)
     int free_max = 0;           // mixed: most free nodes in one part
+    int edge_max = 0;           // mixed: most CSR entries of one part's free nodes
     std::vector<int32_t> rves;  // in scheduling order
     int32_t queue_off = 0;      // offset of its queue in the device queue buffer
 };
@@ -338,6 +339,7 @@ void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
             c.rves.push_back(p);
             c.part_max = std::max(c.part_max, b->rve[p].part_max);
             c.free_max = std::max(c.free_max, b->part_free_max[p]);
+            c.edge_max = std::max(c.edge_max, b->rve[p].part_edge_max);
             c.smem_bytes = kMixedNodeBytes * c.part_max;
         }
         for (auto &c : cls)
@@ -454,8 +456,11 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
             });
             std::sort(fxd[r].begin(), fxd[r].end());
         }
-        int nfree = 0, part_max = 0, free_max = 0;
+        int nfree = 0, part_max = 0, free_max = 0, edge_max = 0;
         for (int r = 0; r < C; ++r) {
+            int pe = 0;
+            for (int i : fr[r]) pe += deg[i];
+            edge_max = std::max(edge_max, pe);
             pf[r] = nfree;
             for (size_t k = 0; k < fr[r].size(); ++k) {
                 owner[fr[r][k]] = r;
@@ -501,6 +506,8 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         R.V0 = V0 ? V0[p] : 1.0;
         R.part_max = part_max;
         R.part_free_max = free_max;
+        R.part_edge_max = edge_max;
+        R.pad = 0;
         b->part_free_max[p] = free_max;
         int32_t pos = 0;
         for (int k = 0; k < n; ++k) {
@@ -765,8 +772,11 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
     } else {
         for (int lead = 1; lead >= 0; --lead) {
             const int block = mixed_block(c, o.block_threads, lead != 0);
-            const size_t smem = lead ? kLeadNodeBytes * c.part_max : c.smem_bytes;
-            const int resident = occupancy_dr_mixed(lead, c.parts, block, smem);
+            const size_t smem = lead ? kLeadNodeBytes * c.part_max
+                                     : mixed_fp32_smem(c.part_max, c.free_max, c.edge_max,
+                                                       b->smem_optin - 16384);
+            const int resident = occupancy_dr_mixed(lead, c.parts, block, smem, c.part_max, c.free_max,
+                                                    c.edge_max);
             if (resident < 1)
                 return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
                                            std::to_string(smem) + " B shared memory fits");
@@ -774,7 +784,8 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
                 if (*timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
                 CUDA_TRY(cudaEventRecord(b->tev[*timed], s));
             }
-            const int e = launch_dr_mixed(M, S, R, P, lead, std::min(nq, resident), c.parts, block, smem, s);
+            const int e = launch_dr_mixed(M, S, R, P, lead, std::min(nq, resident), c.parts, block, smem,
+                                          c.part_max, c.free_max, c.edge_max, s);
             if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
             if (timed) {
                 CUDA_TRY(cudaEventRecord(b->tev[*timed + 1], s));
