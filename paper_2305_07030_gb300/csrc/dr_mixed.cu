@@ -48,16 +48,29 @@ namespace fe2 {
 namespace {
 
 constexpr int kMaxWarps = 16;  // blocks of at most 512 threads
-constexpr int kBufs = 3;       // rotating increment / partial buffers
-// FP32 kernel shared memory per staged node: reference position, three
+constexpr int kLeadBufs = 3;   // lead kernel: rotating partial buffers
+constexpr int kBufs = 4;       // FP32 kernel: rotating increment / partial buffers
+// FP32 kernel shared memory per staged node: reference position, four
 // increment buffers (float4 each), velocity + a.x (float4), a.yz (float2).
 constexpr size_t kFp32NodeBytes = (1 + kBufs + 1) * sizeof(float4) + sizeof(float2);
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Convergence verdict on one evaluation (FP32 kernel): code -1 = go on, else
+// the RVE status; the double-float squared residual and kinetic energy.
+struct Verdict {
+    int code;
+    float r2h, r2l, k2h, k2l;
+};
+
 struct MixedShared {
-    float red[kBufs][kMaxParts * kMaxWarps];  // per-warp residual partials of every CTA,
-                                              // dense: entry (rank * warps + warp)
-    float kred[kBufs][kMaxParts * kMaxWarps]; // kinetic-energy partials
+    // lead kernel: per-warp residual partials of every CTA, dense: entry
+    // (rank * warps + warp)
+    float red[kLeadBufs][kMaxParts * kMaxWarps];
+    float kred[kLeadBufs][kMaxParts * kMaxWarps]; // kinetic-energy partials
+    // FP32 kernel: this CTA's per-warp partials (residual, kinetic energy)
+    float own[kBufs][2][kMaxWarps];
+    Verdict vd[kBufs];                        // verdicts of the judging warp
+    float *ownp[kMaxParts];                   // every CTA's own
     double sig[kMaxParts][9];                 // stress partials, read by rank 0
     double wsum[kMaxWarps][9];                // per-warp stress partials
     float4 *P[kMaxParts];                     // every CTA's position array
@@ -66,6 +79,8 @@ struct MixedShared {
     float *kredp[kMaxParts];                  // every CTA's kred
     double *sigp;                             // rank 0's sig
     int item;
+    int elems;                                // FP32 kernel: elements of this CTA's part
+    int slots;                                // FP32 kernel: row slots of this CTA's part
 };
 
 struct Part {
@@ -194,6 +209,7 @@ __device__ __forceinline__ void map_remote(cg::cluster_group &cl, MixedShared &s
         for (int b = 0; b < kBufs; ++b) sh.Q[b][r] = cl.map_shared_rank(Qb[b], r);
         sh.redp[r] = cl.map_shared_rank(&sh.red[0][0], r);
         sh.kredp[r] = cl.map_shared_rank(&sh.kred[0][0], r);
+        sh.ownp[r] = cl.map_shared_rank(&sh.own[0][0][0], r);
     }
     if (threadIdx.x == 0) sh.sigp = cl.map_shared_rank(&sh.sig[0][0], 0);
 }
@@ -259,7 +275,7 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
     publish(sh, pt, acc, 0.f, false, rb);
     cl.sync();
     const double f_aff = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
-    rb = (rb + 1) % kBufs;
+    rb = (rb + 1) % kLeadBufs;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int i = pt.gidx(k);
         Pl[k] = make_float4(uh[i], uh[n + i], uh[2 * n + i], 0.f);
@@ -285,7 +301,7 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
     publish(sh, pt, acc, 0.f, false, rb);
     cl.sync();
     const double f0 = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
-    rb = (rb + 1) % kBufs;
+    rb = (rb + 1) % kLeadBufs;
     const double f_ref = f_aff > f0 ? f_aff : f0;
     const df thresh2 = df_from_double(dmul(dmul(P.tol, f_ref), dmul(P.tol, f_ref)));
     const df lead2 = df_from_double(dmul(dmul(P.lead_tol, f_ref), dmul(P.lead_tol, f_ref)));
@@ -345,7 +361,7 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         cl.sync();
         r2 = cluster_total(sh.red, rb, pt.C);
         if (want_k) k2 = cluster_total(sh.kred, rb, pt.C);
-        rb = (rb + 1) % kBufs;
+        rb = (rb + 1) % kLeadBufs;
         ++it;
         if (!isfinite(r2.hi)) { status = RVE_NAN; break; }
         if (df_le(r2, thresh2)) { status = RVE_OK; break; }
@@ -385,21 +401,201 @@ __device__ __forceinline__ void edge_increment(const float4 &pi, const float4 &q
     g2 += qref * e2 + dq * (r2 + e2);
 }
 
+// Per-part element tables of the FP32 kernel, in shared memory when they fit
+// (STAGE); otherwise every row is re-read from the global CSR each iteration.
+//
+// Element list: each element with at least one end among this CTA's free
+// nodes appears once. An element between two own free nodes belongs to the
+// row of its lower local index (end a) and is used with the opposite sign by
+// the other row (end b); any other element belongs to the row of its own free
+// end a. Element u holds
+//   K0 = (r, |r|^2), r = x_ref,b - x_ref,a,
+//   K1 = (q_ref, EA, 1/|r|, address of b's increment in buffer 0: shared::cta,
+//        or shared::cluster with bit 0 set when b lives in another CTA),
+//   EI = shared::cta address of a's increment in buffer 0,
+//   TF = the iteration's force increment on a (on b it is -TF, exactly).
+// The reference geometry only changes when the reference state moves.
+// Node rows are laid out ELL-style in slabs of 32 consecutive own free nodes:
+// entry j of node k sits at slot SS[k / 32] + 32 j + k % 32 and holds
+// (element << 1 | 1 if the node is end b), so a warp reads 32 consecutive
+// slots at every step; the entries keep the CSR row order.
+struct Staged {
+    float4 *SG;    // per own free node: (g_ref, 1/m)
+    float4 *K0;    // per element
+    float4 *K1;    // per element
+    float4 *TF;    // per element
+    uint32_t *EI;  // per element
+    uint32_t *NS;  // per slot
+    int *SD;       // per own free node: row length
+    int *EB;       // per own free node: first element of its row
+    int *SS;       // per slab + 1: first slot
+};
+
+// 32-bit shared-memory address of p and its image in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float4 ld_cluster(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float4 ld_local(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a));
+    return v;
+}
+
+// The FP32 increment of edge_increment with the reference geometry taken from
+// an element's K0, K1 (same operations, same order).
+__device__ __forceinline__ void edge_increment_slot(const float4 &qi, const float4 &qj, const float4 &k0,
+                                                    const float4 &k1, float &g0, float &g1, float &g2) {
+    const float r0 = k0.x, r1 = k0.y, r2 = k0.z, lr2 = k0.w;
+    const float qref = k1.x, ea = k1.y, ril = k1.z;
+    const float e0 = qj.x - qi.x, e1 = qj.y - qi.y, e2 = qj.z - qi.z;
+    const float lr = lr2 * ril;
+    const float h = 2.f * (r0 * e0 + r1 * e1 + r2 * e2) + (e0 * e0 + e1 * e1 + e2 * e2);
+    const float rl = rsqrtf(lr2 + h);
+    const float l = (lr2 + h) * rl;
+    const float dq = __fdividef(ea * h * rl * ril, l + lr);
+    g0 += qref * e0 + dq * (r0 + e0);
+    g1 += qref * e1 + dq * (r1 + e1);
+    g2 += qref * e2 + dq * (r2 + e2);
+}
+
+// Whether CSR entry (rank r, local loc) of own free node k is used with the
+// opposite sign: its element belongs to the lower own free end.
+__device__ __forceinline__ bool b_end(int r, int loc, int k, const Part &pt) {
+    return r == pt.me && loc < pt.nfr && loc < k;
+}
+
+// Row lengths and element counts of this CTA's free nodes (first pass), then
+// (thread 0) element offsets and slab bases. The caller synchronises the CTA
+// before the second part.
+__device__ void element_counts(const DevMesh &M, const RveDesc &R, const Part &pt, const int32_t *rowptr,
+                               const Staged &st) {
+    for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+        const int beg = rowptr[pt.f0 + k], deg = rowptr[pt.f0 + k + 1] - beg;
+        int own = 0;
+        for (int e = 0; e < deg; ++e) {
+            const int cp = M.col_part[R.csr0 + beg + e];
+            own += !b_end(cp >> 16, cp & 0xffff, k, pt);
+        }
+        st.SD[k] = deg;
+        st.EB[k] = own;
+    }
+}
+__device__ void element_offsets(MixedShared &sh, const Part &pt, const Staged &st) {
+    int base = 0;
+    for (int k = 0; k < pt.nfr; ++k) {
+        const int c = st.EB[k];
+        st.EB[k] = base;
+        base += c;
+    }
+    sh.elems = base;
+    int slots = 0, s = 0;
+    for (int k0 = 0; k0 < pt.nfr; k0 += 32, ++s) {
+        int w = 0;
+        for (int k = k0; k < k0 + 32 && k < pt.nfr; ++k) w = max(w, st.SD[k]);
+        st.SS[s] = slots;
+        slots += 32 * w;
+    }
+    st.SS[s] = slots;
+    sh.slots = slots;
+}
+
+// Fill the element table from the current reference positions (every CTA's Pl
+// must be final): K0 and K1.xyz always; with `full` also the addresses and the
+// node rows.
+__device__ void element_setup(const MixedShared &sh, const DevMesh &M, const RveDesc &R, const Part &pt,
+                              const int32_t *rowptr, const float4 *Pl, const float4 *Q0,
+                              const Staged &st, bool full) {
+    for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+        const int beg = rowptr[pt.f0 + k], deg = st.SD[k];
+        const float4 pa = Pl[k];
+        int u = st.EB[k];
+        int slot = st.SS[k >> 5] + (k & 31);
+        for (int e = 0; e < deg; ++e, slot += 32) {
+            const int64_t kk = R.csr0 + beg + e;
+            const int cp = M.col_part[kk];
+            const int r = cp >> 16, loc = cp & 0xffff;
+            if (b_end(r, loc, k, pt)) {
+                if (full) {
+                    // the element's index in row loc
+                    const int jb = rowptr[pt.f0 + loc], jd = st.SD[loc];
+                    int v = st.EB[loc];
+                    for (int x = 0; x < jd; ++x) {
+                        const int cq = M.col_part[R.csr0 + jb + x];
+                        const int rq = cq >> 16, lq = cq & 0xffff;
+                        if (rq == pt.me && lq == k) break;
+                        v += !b_end(rq, lq, loc, pt);
+                    }
+                    st.NS[slot] = ((uint32_t)v << 1) | 1u;
+                }
+                continue;
+            }
+            const float4 pb = r == pt.me ? Pl[loc] : sh.P[r][loc];
+            const float2 ei = M.eaf[kk];
+            const float r0 = pb.x - pa.x, r1 = pb.y - pa.y, r2 = pb.z - pa.z;
+            const float lr2 = r0 * r0 + r1 * r1 + r2 * r2;
+            const float ril = rsqrtf(lr2);
+            const float qref = ei.x * (ei.y - ril);
+            uint32_t ab;
+            if (full) {
+                const uint32_t qb = smem_addr(Q0 + loc);
+                ab = r == pt.me ? qb : (cluster_addr(qb, (uint32_t)r) | 1u);
+                st.EI[u] = smem_addr(Q0 + k);
+                st.NS[slot] = (uint32_t)u << 1;
+            } else {
+                ab = __float_as_uint(st.K1[u].w);
+            }
+            st.K0[u] = make_float4(r0, r1, r2, lr2);
+            st.K1[u] = make_float4(qref, ei.x, ril, __uint_as_float(ab));
+            ++u;
+        }
+    }
+}
+
+// Convergence verdict on one evaluation: the double-float total of every
+// CTA's per-warp partials (fixed order: rank, then warp), read through
+// distributed shared memory.
+__device__ __forceinline__ Verdict judge(const MixedShared &sh, const Part &pt, int buf, int64_t done,
+                                         const df &thresh2, bool want_k, int64_t max_iter) {
+    const int nw = (int)(blockDim.x >> 5), total = pt.C * nw, lane = threadIdx.x & 31;
+    df r2 = df_from(0.f), k2 = df_from(0.f);
+    for (int j = lane; j < total; j += 32) {
+        const int r = j / nw, w = j - r * nw;
+        r2 = df_add_f(r2, sh.ownp[r][(buf * 2 + 0) * kMaxWarps + w]);
+        if (want_k) k2 = df_add_f(k2, sh.ownp[r][(buf * 2 + 1) * kMaxWarps + w]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        r2 = df_add(r2, {__shfl_xor_sync(0xffffffffu, r2.hi, o), __shfl_xor_sync(0xffffffffu, r2.lo, o)});
+        if (want_k)
+            k2 = df_add(k2, {__shfl_xor_sync(0xffffffffu, k2.hi, o), __shfl_xor_sync(0xffffffffu, k2.lo, o)});
+    }
+    Verdict v;
+    v.code = !isfinite(r2.hi) ? RVE_NAN : df_le(r2, thresh2) ? RVE_OK : done >= max_iter ? RVE_MAXITER : -1;
+    v.r2h = r2.hi; v.r2l = r2.lo; v.k2h = k2.hi; v.k2l = k2.lo;
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // FP32 kernel: increment iterations, reference refreshes, final state, stress
 // ---------------------------------------------------------------------------
-// Shared-memory staging of one part's CSR rows for the FP32 kernel.
-struct Staged {
-    float4 *SG;  // per own free node: (g_ref, 1/m)
-    int *SR;     // per own free node + 1: row offsets into SC / SE
-    int *SC;     // neighbour as (part << 16 | index in part)
-    float2 *SE;  // (EA, 1/L)
-};
-
 template <bool STAGE>
 __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
                          const DevResults &O, const SolveParams &P, int p, float4 *Pl,
-                         float4 *const *Qb, float4 *SV, float2 *SA, const Staged &st, int &rb) {
+                         float4 *const *Qb, float4 *SV, float2 *SA, const Staged &st, int elem_cap,
+                         int slot_cap, uint32_t bstride) {
     const RveDesc R = M.rve[p];
     const Part pt = make_part(M, R, p, (int)cl.block_rank(), (int)cl.num_blocks());
     const int n = R.n_nodes, m = pt.m();
@@ -427,13 +623,17 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         const double dt64 = dmul(P.alpha, R.dtc);
         const float dtf = (float)dt64, hdtf = (float)dmul(0.5, dt64), cf = (float)R.c;
         const int K = P.rebase_every > 0 ? P.rebase_every : 512;
-        // lanes per node: as many as the CTA size allows for this RVE's largest part.
-        // Node k's velocity and acceleration are owned by lane 0 of group k in
-        // every phase, so consecutive phases need no barrier between them.
+        // lanes per node: with the element table one (element forces are spread
+        // over all threads, node sums are short); otherwise as many as the CTA
+        // size allows for this RVE's largest part. Node k's velocity and
+        // acceleration are owned by lane 0 of group k in every phase, so
+        // consecutive phases need no barrier between them.
         int lanes = 1;
-        while (lanes < 4 && (int)blockDim.x >= 2 * lanes * R.part_free_max) lanes *= 2;
+        while (!STAGE && lanes < 4 && (int)blockDim.x >= 2 * lanes * R.part_free_max) lanes *= 2;
         const int L = lanes;
         const int sub = threadIdx.x & (L - 1), grp = threadIdx.x / L, ngrp = blockDim.x / L;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const bool judge_warp = warp == (int)(blockDim.x >> 5) - 1;
         // x_ref = X + u (FP32 rounding of the double-float sum), increments zero;
         // g_ref = fg from the lead's last force evaluation at exactly this state
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
@@ -448,29 +648,40 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             if (k < pt.nfr) {
                 SV[k] = make_float4(vh[i], vh[n + i], vh[2 * n + i], ah[i]);
                 SA[k] = make_float2(ah[n + i], ah[2 * n + i]);
-                if (STAGE) {
-                    st.SG[k] = make_float4(fg[i], fg[n + i], fg[2 * n + i], imh[i]);
-                    st.SR[k] = rowptr[i] - rowptr[pt.f0];
-                }
+                if (STAGE) st.SG[k] = make_float4(fg[i], fg[n + i], fg[2 * n + i], imh[i]);
             }
         }
         if (STAGE) {
-            const int e0 = rowptr[pt.f0], ne = rowptr[pt.f0 + pt.nfr] - e0;
-            if (threadIdx.x == 0) st.SR[pt.nfr] = ne;
-            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-                st.SC[e] = M.col_part[R.csr0 + e0 + e];
-                st.SE[e] = M.eaf[R.csr0 + e0 + e];
-            }
+            element_counts(M, R, pt, rowptr, st);
+            __syncthreads();
+            if (threadIdx.x == 0) element_offsets(sh, pt, st);
         }
         cl.sync();
+        int n_el = 0;
+        if (STAGE) {
+            // The capacities are sized on the host for every part. Should a
+            // part not fit, every CTA of the cluster sees it (so all leave the
+            // loop together) and the RVE is reported failed.
+            bool over = false;
+            for (int r = 0; r < pt.C; ++r)
+                over |= *cl.map_shared_rank(&sh.elems, r) > elem_cap ||
+                        *cl.map_shared_rank(&sh.slots, r) > slot_cap;
+            if (over) status = RVE_NAN;
+            else element_setup(sh, M, R, pt, rowptr, Pl, Qb[0], st, true);
+            n_el = sh.elems;
+        }
         const int64_t first = it;  // evaluation index of the first FP32 iteration
         int64_t chk = first;       // next evaluation whose residual is still untested
         int chkb = 0;              // its buffer
+        // the verdict the judging warp wrote in the previous iteration
+        bool vpend = false;
+        int64_t veval = 0;
+        int vbuf = 0;
         int since = 0;
         const int32_t *colp = M.col_part + R.csr0;
         const float2 *eafp = M.eaf + R.csr0;
         int b = 0, bp = kBufs - 1;  // buffers of evaluation nidx and nidx - 1
-        for (int64_t nidx = first;; ++nidx, bp = b, b = (b + 1 == kBufs ? 0 : b + 1)) {
+        for (int64_t nidx = first; status == RVE_PENDING; ++nidx, bp = b, b = (b + 1 == kBufs ? 0 : b + 1)) {
             // partial velocity update; displacement increment into buffer b
             {
                 const float4 *prev = Qb[bp];
@@ -488,38 +699,53 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     cur[k] = make_float4(d.x + dtf * w0, d.y + dtf * w1, d.z + dtf * w2, 0.f);
                 }
             }
+            const bool rebase = since >= K;
             cluster_arrive();
-            // residual test of evaluation nidx-2 while the barrier completes
-            bool stop = false;
+            // Residual test of evaluation nidx-2 while the barrier completes: by
+            // one warp per CTA, whose verdict the others read after the next
+            // barrier (buffers rotate through four, so the state of the tested
+            // evaluation is intact until then); by every warp before a rebase.
+            bool tnow = false;
+            int64_t teval = 0;
+            int tbuf = 0;
+            Verdict mine = {-1, 0.f, 0.f, 0.f, 0.f};
             if (chk <= nidx - 2) {
-                r2 = cluster_total(sh.red, chkb, pt.C);
-                if (want_k) k2 = cluster_total(sh.kred, chkb, pt.C);
-                const int64_t done = chk + 1;
-                if (!isfinite(r2.hi)) { status = RVE_NAN; stop = true; }
-                else if (df_le(r2, thresh2)) { status = RVE_OK; stop = true; }
-                else if (done >= P.max_iter) { status = RVE_MAXITER; stop = true; }
-                if (stop) { fin = chkb; it = done; }
+                if (rebase || judge_warp) mine = judge(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
+                if (!rebase && judge_warp && lane == 0) sh.vd[b] = mine;
+                tnow = true; teval = chk; tbuf = chkb;
                 ++chk;
                 chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
             }
             cluster_wait();
-            if (stop) break;
-            float4 *cur = Qb[b];
-            float rs = 0.f, kes = 0.f;
-            if (since >= K) {
-                // the reference moves: every earlier evaluation must be tested first
-                if (chk == nidx - 1) {
-                    r2 = cluster_total(sh.red, chkb, pt.C);
-                    if (want_k) k2 = cluster_total(sh.kred, chkb, pt.C);
-                    const int64_t done = chk + 1;
-                    if (!isfinite(r2.hi)) { status = RVE_NAN; stop = true; }
-                    else if (df_le(r2, thresh2)) { status = RVE_OK; stop = true; }
-                    else if (done >= P.max_iter) { status = RVE_MAXITER; stop = true; }
-                    if (stop) { fin = chkb; it = done; }
+            Verdict stopv = {-1, 0.f, 0.f, 0.f, 0.f};
+            int64_t seval = 0;
+            int sbuf = 0;
+            if (vpend) {
+                const Verdict v = sh.vd[bp];
+                if (v.code >= 0) { stopv = v; seval = veval; sbuf = vbuf; }
+            }
+            vpend = false;
+            if (stopv.code < 0 && rebase) {
+                if (tnow && mine.code >= 0) { stopv = mine; seval = teval; sbuf = tbuf; }
+                else if (chk == nidx - 1) {
+                    // the reference moves: every earlier evaluation is tested first
+                    mine = judge(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
+                    if (mine.code >= 0) { stopv = mine; seval = chk; sbuf = chkb; }
                     ++chk;
                     chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
                 }
-                if (stop) break;
+            }
+            if (stopv.code >= 0) {
+                status = stopv.code;
+                fin = sbuf;
+                it = seval + 1;
+                r2 = {stopv.r2h, stopv.r2l};
+                k2 = {stopv.k2h, stopv.k2l};
+                break;
+            }
+            float4 *cur = Qb[b];
+            float rs = 0.f, kes = 0.f;
+            if (rebase) {
                 // fold the increment into the double-float displacement; stage
                 // double-float displacements (hi in Pl, lo in buffer b)
                 for (int k = threadIdx.x; k < m; k += blockDim.x) {
@@ -556,6 +782,7 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     cur[k] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 cl.sync();
+                if (STAGE) element_setup(sh, M, R, pt, rowptr, Pl, Qb[0], st, false);
                 for (int k = grp; k < pt.nfr; k += ngrp) {
                     if (sub != 0) continue;
                     const int i = pt.f0 + k;
@@ -572,59 +799,34 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                 }
                 since = 0;
             } else {
-                // L lanes share a node's edges (lane s takes edges s, s+L, ...,
-                // two at a time) and combine with shuffles; L is fixed per RVE so
-                // its result does not depend on the launch it runs in.
-                for (int kb = 0; kb < pt.nfr; kb += ngrp) {
-                    const int k = kb + grp;
-                    const bool valid = k < pt.nfr;
-                    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-                    if (valid) {
-                        const int i = pt.f0 + k;
-                        const float4 pi = Pl[k], qi = cur[k];
-                        // rows from shared memory (STAGE) or from global memory
-                        const int32_t *cpp = STAGE ? st.SC : colp;
-                        const float2 *epp = STAGE ? st.SE : eafp;
-                        const int end = STAGE ? st.SR[k + 1] : rowptr[i + 1];
-                        int e = (STAGE ? st.SR[k] : rowptr[i]) + sub;
-                        for (; e + L < end; e += 2 * L) {
-                            const int ca = STAGE ? cpp[e] : __ldg(cpp + e);
-                            const int cb = STAGE ? cpp[e + L] : __ldg(cpp + e + L);
-                            const float2 ea = STAGE ? epp[e] : __ldg(epp + e);
-                            const float2 eb = STAGE ? epp[e + L] : __ldg(epp + e + L);
-                            const int ra = ca >> 16, la = ca & 0xffff, rb2 = cb >> 16, lb = cb & 0xffff;
-                            const float4 pa = ra == pt.me ? Pl[la] : sh.P[ra][la];
-                            const float4 qa = ra == pt.me ? cur[la] : sh.Q[b][ra][la];
-                            const float4 pb = rb2 == pt.me ? Pl[lb] : sh.P[rb2][lb];
-                            const float4 qb = rb2 == pt.me ? cur[lb] : sh.Q[b][rb2][lb];
-                            edge_increment(pi, qi, pa, qa, ea, g0, g1, g2);
-                            edge_increment(pi, qi, pb, qb, eb, g0, g1, g2);
-                        }
-                        if (e < end) {
-                            const int ca = STAGE ? cpp[e] : __ldg(cpp + e);
-                            const float2 ea = STAGE ? epp[e] : __ldg(epp + e);
-                            const int ra = ca >> 16, la = ca & 0xffff;
-                            const float4 pa = ra == pt.me ? Pl[la] : sh.P[ra][la];
-                            const float4 qa = ra == pt.me ? cur[la] : sh.Q[b][ra][la];
-                            edge_increment(pi, qi, pa, qa, ea, g0, g1, g2);
-                        }
+                vpend = tnow; veval = teval; vbuf = tbuf;
+                const uint32_t boff = (uint32_t)b * bstride;
+                if (STAGE) {
+                    // element forces, spread evenly over the CTA's threads
+                    for (int u = threadIdx.x; u < n_el; u += blockDim.x) {
+                        const float4 k0 = st.K0[u], k1 = st.K1[u];
+                        const float4 qa = ld_local(st.EI[u] + boff);
+                        const uint32_t ab = __float_as_uint(k1.w);
+                        const float4 qb = (ab & 1u) ? ld_cluster((ab & ~1u) + boff) : ld_local(ab + boff);
+                        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+                        edge_increment_slot(qa, qb, k0, k1, t0, t1, t2);
+                        st.TF[u] = make_float4(t0, t1, t2, 0.f);
                     }
-                    for (int o = 1; o < L; o <<= 1) {
-                        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-                        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-                        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
-                    }
-                    if (valid && sub == 0) {
-                        const int i = pt.f0 + k;
-                        float im;
-                        if (STAGE) {
-                            const float4 gr = st.SG[k];
-                            g0 += gr.x; g1 += gr.y; g2 += gr.z;
-                            im = gr.w;
-                        } else {
-                            g0 += fg[i]; g1 += fg[n + i]; g2 += fg[2 * n + i];
-                            im = imh[i];
+                    __syncthreads();
+                    // node sums in CSR row order, then the velocity update
+                    for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+                        const int deg = st.SD[k];
+                        int sl = st.SS[k >> 5] + (k & 31);
+                        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+                        for (int j = 0; j < deg; ++j, sl += 32) {
+                            const uint32_t w = st.NS[sl];
+                            const float4 t = st.TF[w >> 1];
+                            if (w & 1u) { g0 -= t.x; g1 -= t.y; g2 -= t.z; }
+                            else { g0 += t.x; g1 += t.y; g2 += t.z; }
                         }
+                        const float4 gr = st.SG[k];
+                        g0 += gr.x; g1 += gr.y; g2 += gr.z;
+                        const float im = gr.w;
                         const float4 va = SV[k];
                         float w0 = va.x, w1 = va.y, w2 = va.z;
                         const float a0 = g0 * im - cf * w0;
@@ -636,10 +838,71 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                         rs += g0 * g0 + g1 * g1 + g2 * g2;
                         if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
                     }
+                } else {
+                    // L lanes share a node's edges (lane s takes edges s, s+L, ...,
+                    // two at a time) and combine with shuffles; L is fixed per RVE
+                    // so its result does not depend on the launch it runs in.
+                    for (int kb = 0; kb < pt.nfr; kb += ngrp) {
+                        const int k = kb + grp;
+                        const bool valid = k < pt.nfr;
+                        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+                        if (valid) {
+                            const float4 qi = cur[k];
+                            const int i = pt.f0 + k;
+                            const float4 pi = Pl[k];
+                            const int end = rowptr[i + 1];
+                            int e = rowptr[i] + sub;
+                            for (; e + L < end; e += 2 * L) {
+                                const int ca = __ldg(colp + e), cb = __ldg(colp + e + L);
+                                const float2 ea = __ldg(eafp + e), eb = __ldg(eafp + e + L);
+                                const int ra = ca >> 16, la = ca & 0xffff, rb2 = cb >> 16, lb = cb & 0xffff;
+                                const float4 pa = ra == pt.me ? Pl[la] : sh.P[ra][la];
+                                const float4 qa = ra == pt.me ? cur[la] : sh.Q[b][ra][la];
+                                const float4 pb = rb2 == pt.me ? Pl[lb] : sh.P[rb2][lb];
+                                const float4 qb = rb2 == pt.me ? cur[lb] : sh.Q[b][rb2][lb];
+                                edge_increment(pi, qi, pa, qa, ea, g0, g1, g2);
+                                edge_increment(pi, qi, pb, qb, eb, g0, g1, g2);
+                            }
+                            if (e < end) {
+                                const int ca = __ldg(colp + e);
+                                const float2 ea = __ldg(eafp + e);
+                                const int ra = ca >> 16, la = ca & 0xffff;
+                                const float4 pa = ra == pt.me ? Pl[la] : sh.P[ra][la];
+                                const float4 qa = ra == pt.me ? cur[la] : sh.Q[b][ra][la];
+                                edge_increment(pi, qi, pa, qa, ea, g0, g1, g2);
+                            }
+                        }
+                        for (int o = 1; o < L; o <<= 1) {
+                            g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+                            g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+                            g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+                        }
+                        if (valid && sub == 0) {
+                            const int i = pt.f0 + k;
+                            g0 += fg[i]; g1 += fg[n + i]; g2 += fg[2 * n + i];
+                            const float im = imh[i];
+                            const float4 va = SV[k];
+                            float w0 = va.x, w1 = va.y, w2 = va.z;
+                            const float a0 = g0 * im - cf * w0;
+                            const float a1 = g1 * im - cf * w1;
+                            const float a2 = g2 * im - cf * w2;
+                            w0 += hdtf * a0; w1 += hdtf * a1; w2 += hdtf * a2;
+                            SV[k] = make_float4(w0, w1, w2, a0);
+                            SA[k] = make_float2(a1, a2);
+                            rs += g0 * g0 + g1 * g1 + g2 * g2;
+                            if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
+                        }
+                    }
                 }
             }
-            // publish this evaluation's partials; tested two iterations later
-            publish(sh, pt, rs, kes, want_k, b);
+            // this evaluation's per-warp partials, in this CTA's own buffer b
+            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+            if (want_k)
+                for (int o = 16; o > 0; o >>= 1) kes += __shfl_xor_sync(0xffffffffu, kes, o);
+            if (lane == 0) {
+                sh.own[b][0][warp] = rs;
+                if (want_k) sh.own[b][1][warp] = kes;
+            }
             ++since;
         }
     }
@@ -718,7 +981,7 @@ __global__ void __launch_bounds__(512) dr_mixed_lead_kernel(DevMesh M, DevState 
     __shared__ MixedShared sh;
     cg::cluster_group cl = cg::this_cluster();
     float4 *Pl = dsm, *Q0 = dsm + part_cap;
-    float4 *Qb[kBufs] = {Q0, Q0, Q0};
+    float4 *Qb[kBufs] = {Q0, Q0, Q0, Q0};
     map_remote(cl, sh, Pl, Qb, (int)cl.num_blocks());
     int rb = 0;
     for (;;) {
@@ -731,28 +994,45 @@ __global__ void __launch_bounds__(512) dr_mixed_lead_kernel(DevMesh M, DevState 
 template <bool STAGE>
 __global__ void __launch_bounds__(512, 1) dr_mixed_fp32_kernel(DevMesh M, DevState S, DevResults O,
                                                                SolveParams P, int part_cap,
-                                                               int free_cap, int edge_cap) {
+                                                               int free_cap, int elem_cap,
+                                                               int slot_cap) {
     extern __shared__ __align__(16) float4 dsm[];
     __shared__ MixedShared sh;
     cg::cluster_group cl = cg::this_cluster();
     float4 *Pl = dsm;
-    float4 *Qb[kBufs] = {dsm + part_cap, dsm + 2 * part_cap, dsm + 3 * part_cap};
-    float4 *SV = dsm + 4 * part_cap;
-    float2 *SA = reinterpret_cast<float2 *>(dsm + 5 * part_cap);
+    float4 *Qb[kBufs];
+    for (int b = 0; b < kBufs; ++b) Qb[b] = dsm + (1 + b) * part_cap;
+    float4 *SV = dsm + (1 + kBufs) * part_cap;
+    float2 *SA = reinterpret_cast<float2 *>(dsm + (2 + kBufs) * part_cap);
     Staged st = {};
     if (STAGE) {
+        // layout as in mixed_fp32_smem
         char *base = reinterpret_cast<char *>(dsm) + align16(kFp32NodeBytes * part_cap);
         st.SG = reinterpret_cast<float4 *>(base);
-        st.SE = reinterpret_cast<float2 *>(base + 16 * (size_t)free_cap);
-        st.SC = reinterpret_cast<int *>(base + 16 * (size_t)free_cap + 8 * (size_t)edge_cap);
-        st.SR = reinterpret_cast<int *>(base + 16 * (size_t)free_cap + 12 * (size_t)edge_cap);
+        base += 16 * (size_t)free_cap;
+        st.K0 = reinterpret_cast<float4 *>(base);
+        base += 16 * (size_t)elem_cap;
+        st.K1 = reinterpret_cast<float4 *>(base);
+        base += 16 * (size_t)elem_cap;
+        st.TF = reinterpret_cast<float4 *>(base);
+        base += 16 * (size_t)elem_cap;
+        st.EI = reinterpret_cast<uint32_t *>(base);
+        base += 4 * (size_t)elem_cap;
+        st.NS = reinterpret_cast<uint32_t *>(base);
+        base += 4 * (size_t)slot_cap;
+        st.SD = reinterpret_cast<int *>(base);
+        base += 4 * (size_t)free_cap;
+        st.EB = reinterpret_cast<int *>(base);
+        base += 4 * (size_t)free_cap;
+        st.SS = reinterpret_cast<int *>(base);
     }
     map_remote(cl, sh, Pl, Qb, (int)cl.num_blocks());
-    int rb = 0;
+    const uint32_t bstride = (uint32_t)(sizeof(float4) * part_cap);
     for (;;) {
         const int item = next_item(cl, sh, P.counter + 1);
         if (item >= P.queue_len) return;
-        fp32_rve<STAGE>(cl, sh, M, S, O, P, P.queue[item], Pl, Qb, SV, SA, st, rb);
+        fp32_rve<STAGE>(cl, sh, M, S, O, P, P.queue[item], Pl, Qb, SV, SA, st, elem_cap, slot_cap,
+                        bstride);
     }
 }
 
@@ -780,16 +1060,17 @@ void prepare(K kernel, size_t smem) {
 }
 }  // namespace
 
-size_t mixed_fp32_smem(int part_cap, int free_cap, int edge_cap, size_t limit) {
+size_t mixed_fp32_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, size_t limit) {
     const size_t plain = kFp32NodeBytes * (size_t)part_cap;
-    const size_t staged = align16(align16(plain) + 16 * (size_t)free_cap + 12 * (size_t)edge_cap +
-                                  4 * ((size_t)free_cap + 1));
+    const size_t F = (size_t)free_cap, U = (size_t)elem_cap, S = (size_t)slot_cap;
+    const size_t staged =
+        align16(align16(plain) + 16 * F + 3 * 16 * U + 4 * U + 4 * S + 2 * 4 * F + 4 * (F / 32 + 2));
     return staged <= limit ? staged : plain;
 }
 
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
                     int lead, int clusters, int parts, int block, size_t smem, int part_cap,
-                    int free_cap, int edge_cap, void *stream) {
+                    int free_cap, int elem_cap, int slot_cap, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = mixed_config(clusters, parts, block, smem, attr, st);
@@ -801,20 +1082,17 @@ int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, co
     } else if (smem > kFp32NodeBytes * (size_t)part_cap) {
         prepare(dr_mixed_fp32_kernel<true>, smem);
         e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel<true>, m, s, r, p, part_cap, free_cap,
-                               edge_cap);
+                               elem_cap, slot_cap);
     } else {
         prepare(dr_mixed_fp32_kernel<false>, smem);
         e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel<false>, m, s, r, p, part_cap, free_cap,
-                               edge_cap);
+                               elem_cap, slot_cap);
     }
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 
-int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap, int free_cap,
-                       int edge_cap) {
-    (void)free_cap;
-    (void)edge_cap;
+int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = mixed_config(parts * 64, parts, block, smem, attr, nullptr);
     int n = 0;

@@ -39,8 +39,8 @@ struct RveDesc {
     double V0;        // reference volume
     int32_t part_max;       // largest part (nodes), sizes the shared memory
     int32_t part_free_max;  // most free nodes in one part
-    int32_t part_edge_max;  // most CSR entries of one part's free nodes
-    int32_t pad;
+    int32_t part_elem_max;  // FP32 kernel: most table elements of one part
+    int32_t part_slot_max;  // FP32 kernel: most row slots (ELL, 32-node slabs) of one part
 };
 
 // Read-only, create-time arrays.
@@ -118,14 +118,14 @@ int launch_dr_fp64(const DevMesh &m, const DevState &s, const DevResults &r,
 // the FP32 phase (lead = 0).
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r,
                     const SolveParams &p, int lead, int clusters, int parts, int block,
-                    size_t smem, int part_cap, int free_cap, int edge_cap, void *stream);
+                    size_t smem, int part_cap, int free_cap, int elem_cap, int slot_cap,
+                    void *stream);
 // Dynamic shared memory of the FP32 kernel for a class: the staged node state,
-// plus each part's CSR rows when they fit within `limit` bytes.
-size_t mixed_fp32_smem(int part_cap, int free_cap, int edge_cap, size_t limit);
+// plus each part's element table and rows when they fit within `limit` bytes.
+size_t mixed_fp32_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, size_t limit);
 // Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.
 int occupancy_dr_fp64(int smem_positions, int block, size_t smem);
-int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap, int free_cap,
-                       int edge_cap);
+int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap);
 
 // Naive comparator: scratch sized for the largest RVE, and one RVE's solve.
 struct NaiveScratch {

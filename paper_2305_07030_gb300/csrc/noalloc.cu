@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kNaThreads) k_noalloc_solve(NaArgs A, SolvePar
         R.node0 = 0; R.rp0 = 0; R.csr0 = 0; R.elem0 = 0;
         R.n_nodes = n; R.n_free = nf; R.n_elems = E; R.n_parts = 1;
         R.dtc = t; R.c = A.c; R.V0 = A.V0; R.part_max = n; R.part_free_max = nf;
-        R.part_edge_max = 2 * E; R.pad = 0;
+        R.part_elem_max = 0; R.part_slot_max = 0;
         *rve = R;
     }
     __syncthreads();

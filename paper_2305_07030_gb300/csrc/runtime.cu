@@ -64,7 +64,8 @@ struct SizeClass {
     size_t smem_bytes = 0;      // dynamic shared memory per CTA
     int part_max = 0;           // mixed: largest part (nodes)
     int free_max = 0;           // mixed: most free nodes in one part
-    int edge_max = 0;           // mixed: most CSR entries of one part's free nodes
+    int elem_max = 0;           // mixed: most FP32-kernel table elements of one part
+    int slot_max = 0;           // mixed: most FP32-kernel row slots of one part
     std::vector<int32_t> rves;  // in scheduling order
     int32_t queue_off = 0;      // offset of its queue in the device queue buffer
 };
@@ -260,10 +261,10 @@ namespace {
 bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
 // Shared-memory bytes per staged node of the mixed solver's FP32 kernel
-// (reference position and three rotating increment buffers, float4 each;
+// (reference position and four rotating increment buffers, float4 each;
 // velocity and acceleration, float4 + float2) and of its lead kernel
 // (double-float displacement, two float4).
-constexpr size_t kMixedNodeBytes = 88;
+constexpr size_t kMixedNodeBytes = 104;
 constexpr size_t kLeadNodeBytes = 32;
 
 // Number of cluster CTAs for an RVE of n nodes in the mixed solver: a power
@@ -339,7 +340,8 @@ void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
             c.rves.push_back(p);
             c.part_max = std::max(c.part_max, b->rve[p].part_max);
             c.free_max = std::max(c.free_max, b->part_free_max[p]);
-            c.edge_max = std::max(c.edge_max, b->rve[p].part_edge_max);
+            c.elem_max = std::max(c.elem_max, b->rve[p].part_elem_max);
+            c.slot_max = std::max(c.slot_max, b->rve[p].part_slot_max);
             c.smem_bytes = kMixedNodeBytes * c.part_max;
         }
         for (auto &c : cls)
@@ -456,11 +458,8 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
             });
             std::sort(fxd[r].begin(), fxd[r].end());
         }
-        int nfree = 0, part_max = 0, free_max = 0, edge_max = 0;
+        int nfree = 0, part_max = 0, free_max = 0;
         for (int r = 0; r < C; ++r) {
-            int pe = 0;
-            for (int i : fr[r]) pe += deg[i];
-            edge_max = std::max(edge_max, pe);
             pf[r] = nfree;
             for (size_t k = 0; k < fr[r].size(); ++k) {
                 owner[fr[r][k]] = r;
@@ -506,8 +505,30 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         R.V0 = V0 ? V0[p] : 1.0;
         R.part_max = part_max;
         R.part_free_max = free_max;
-        R.part_edge_max = edge_max;
-        R.pad = 0;
+        // FP32 kernel tables per part: elements with an end among the part's
+        // free nodes, once each (an element between two of them counted at its
+        // lower local index), and row slots in slabs of 32 free nodes, each 32
+        // slots wide per entry of its longest row
+        int elem_max = 0, slot_max = 0;
+        for (int r = 0; r < C; ++r) {
+            int elems = 0, slots = 0;
+            for (size_t k = 0; k < fr[r].size(); ++k) {
+                const int i = fr[r][k];
+                for (const auto &pr : rows[i]) {
+                    const int j = pr.first;
+                    elems += !(owner[j] == r && !fx[j] && local[j] < (int)k);
+                }
+            }
+            for (size_t k0 = 0; k0 < fr[r].size(); k0 += 32) {
+                int w = 0;
+                for (size_t k = k0; k < k0 + 32 && k < fr[r].size(); ++k) w = std::max(w, deg[fr[r][k]]);
+                slots += 32 * w;
+            }
+            elem_max = std::max(elem_max, elems);
+            slot_max = std::max(slot_max, slots);
+        }
+        R.part_elem_max = elem_max;
+        R.part_slot_max = slot_max;
         b->part_free_max[p] = free_max;
         int32_t pos = 0;
         for (int k = 0; k < n; ++k) {
@@ -773,10 +794,9 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
         for (int lead = 1; lead >= 0; --lead) {
             const int block = mixed_block(c, o.block_threads, lead != 0);
             const size_t smem = lead ? kLeadNodeBytes * c.part_max
-                                     : mixed_fp32_smem(c.part_max, c.free_max, c.edge_max,
+                                     : mixed_fp32_smem(c.part_max, c.free_max, c.elem_max, c.slot_max,
                                                        b->smem_optin - 16384);
-            const int resident = occupancy_dr_mixed(lead, c.parts, block, smem, c.part_max, c.free_max,
-                                                    c.edge_max);
+            const int resident = occupancy_dr_mixed(lead, c.parts, block, smem, c.part_max);
             if (resident < 1)
                 return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
                                            std::to_string(smem) + " B shared memory fits");
@@ -785,7 +805,7 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
                 CUDA_TRY(cudaEventRecord(b->tev[*timed], s));
             }
             const int e = launch_dr_mixed(M, S, R, P, lead, std::min(nq, resident), c.parts, block, smem,
-                                          c.part_max, c.free_max, c.edge_max, s);
+                                          c.part_max, c.free_max, c.elem_max, c.slot_max, s);
             if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
             if (timed) {
                 CUDA_TRY(cudaEventRecord(b->tev[*timed + 1], s));

@@ -93,6 +93,29 @@ def test_mixed_within_tolerance_or_rounding_envelope():
     assert sum(1 for row in rows if row[3] <= 1e-6) >= 2
 
 
+def test_mixed_unstaged_fallback(monkeypatch):
+    """Parts too large for the FP32 kernel's shared-memory element table run
+    the fallback that re-reads the CSR rows every iteration: with the
+    node-per-CTA target raised, a 2000-node and a 700-node RVE each run in a
+    single CTA, and their size class's tables do not fit."""
+    monkeypatch.setenv("FE2_NODES_PER_CTA", "8192")
+    w = _workload([2000, 700], seed=20)
+    env = envelope_batch(w)
+    with Batch(w.nets, damping=w.damping) as b:
+        assert list(b.parts()) == [1, 1]
+        b.solve(w.F, precision="mixed", tol=1e-8)
+        out = b.stress()
+        u = b.displacement()
+        off = b.node_off
+    for p, (r, spread) in enumerate(env):
+        res, s_at_u = check_equilibrium(w.nets[p], w.F[p], u[off[p]:off[p + 1]], r["f_ref"], 1e-8)
+        e = rel_err(out["sigma"][p], r["sigma"])
+        assert out["status"][p] == "OK"
+        assert res <= 1.5e-8, (p, res)
+        assert rel_err(out["sigma"][p], s_at_u) <= 1e-12
+        assert e <= (1e-5 if spread <= 1e-6 else 10.0 * spread), (p, e, spread)
+
+
 def test_single_512_node_rve_both_modes():
     """The 512-node RVE with EA = 1 and F = diag(1.05, 1, 1)."""
     w = ri.single_rve_512()
