@@ -53,6 +53,9 @@ constexpr int kBufs = 4;       // FP32 kernel: rotating increment / partial buff
 // FP32 kernel shared memory per staged node: reference position, four
 // increment buffers (float4 each), velocity + a.x (float4), a.yz (float2).
 constexpr size_t kFp32NodeBytes = (1 + kBufs + 1) * sizeof(float4) + sizeof(float2);
+// Lead kernel shared memory per node without the element table: one
+// double-float displacement (hi, lo float4); with the table, two of them.
+constexpr size_t kLeadPlainNodeBytes = 2 * sizeof(float4);
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Convergence verdict on one evaluation (FP32 kernel): code -1 = go on, else
@@ -223,162 +226,6 @@ __device__ __forceinline__ int next_item(cg::cluster_group &cl, MixedShared &sh,
     return item;
 }
 
-// ---------------------------------------------------------------------------
-// lead kernel: setup (Algorithm 1 lines up to the loop) and the double-float
-// iterations
-// ---------------------------------------------------------------------------
-__device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
-                         const DevResults &O, const SolveParams &P, int p, float4 *Pl, float4 *Q0,
-                         int &rb) {
-    const RveDesc R = M.rve[p];
-    const Part pt = make_part(M, R, p, (int)cl.block_rank(), (int)cl.num_blocks());
-    const int n = R.n_nodes, m = pt.m();
-    const int64_t n0 = R.node0, b3 = 3 * n0;
-    const int32_t *rowptr = M.rowptr + R.rp0;
-    double F[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) F[k] = P.F[9 * (int64_t)p + k];
-    float *uh = S.uh + b3, *ul = S.ul + b3, *vh = S.vh + b3, *vl = S.vl + b3;
-    float *ah = S.ah + b3, *al = S.al + b3, *fg = S.fg + b3;
-    const float *imh = M.imh + n0, *iml = M.iml + n0;
-    const bool want_k = P.want_ke != 0;
-
-    // affine displacement (F - I) X for f_ref, and the initial displacement
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        const int i = pt.gidx(k);
-        const double X[3] = {M.X0[n0 + i], M.X1[n0 + i], M.X2[n0 + i]};
-        const double *uw[3] = {S.u0 + n0, S.u1 + n0, S.u2 + n0};
-        df ua[3];
-        const bool fixed = k >= pt.nfr;
-        for (int r = 0; r < 3; ++r) {
-            const double xa = dadd(dadd(dmul(F[3 * r], X[0]), dmul(F[3 * r + 1], X[1])), dmul(F[3 * r + 2], X[2]));
-            const double uaff = dsub(xa, X[r]);
-            ua[r] = df_from_double(uaff);
-            double u;
-            if (fixed || P.init == 1) u = uaff;
-            else if (P.init == 2) u = uw[r][i];
-            else u = 0.0;
-            const df ud = df_from_double(u);
-            uh[r * n + i] = ud.hi;
-            ul[r * n + i] = ud.lo;
-        }
-        Pl[k] = make_float4(ua[0].hi, ua[1].hi, ua[2].hi, 0.f);
-        Q0[k] = make_float4(ua[0].lo, ua[1].lo, ua[2].lo, 0.f);
-    }
-    cl.sync();
-    float acc = 0.f;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        df g0, g1, g2;
-        gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g0, g1, g2);
-        acc += g0.hi * g0.hi + g1.hi * g1.hi + g2.hi * g2.hi;
-    }
-    publish(sh, pt, acc, 0.f, false, rb);
-    cl.sync();
-    const double f_aff = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
-    rb = (rb + 1) % kLeadBufs;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        const int i = pt.gidx(k);
-        Pl[k] = make_float4(uh[i], uh[n + i], uh[2 * n + i], 0.f);
-        Q0[k] = make_float4(ul[i], ul[n + i], ul[2 * n + i], 0.f);
-    }
-    cl.sync();
-    acc = 0.f;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        df g[3];
-        gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g[0], g[1], g[2]);
-        acc += g[0].hi * g[0].hi + g[1].hi * g[1].hi + g[2].hi * g[2].hi;
-        if (k < pt.nfr) {
-            const int i = pt.gidx(k);
-            const df im = {imh[i], iml[i]};
-            for (int r = 0; r < 3; ++r) {
-                const df a = df_mul(g[r], im);
-                ah[r * n + i] = a.hi; al[r * n + i] = a.lo;
-                vh[r * n + i] = 0.f; vl[r * n + i] = 0.f;
-                fg[r * n + i] = g[r].hi;
-            }
-        }
-    }
-    publish(sh, pt, acc, 0.f, false, rb);
-    cl.sync();
-    const double f0 = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
-    rb = (rb + 1) % kLeadBufs;
-    const double f_ref = f_aff > f0 ? f_aff : f0;
-    const df thresh2 = df_from_double(dmul(dmul(P.tol, f_ref), dmul(P.tol, f_ref)));
-    const df lead2 = df_from_double(dmul(dmul(P.lead_tol, f_ref), dmul(P.lead_tol, f_ref)));
-    const double dt64 = dmul(P.alpha, R.dtc);
-    const df dt = df_from_double(dt64), hdt = df_from_double(dmul(0.5, dt64));
-    const df cdf = df_from_double(R.c);
-
-    int64_t it = 0;
-    int status = RVE_PENDING;
-    df r2 = df_from(0.f), k2 = df_from(0.f);
-    // L lanes share a node's edges; lane 0 of group k owns node k's state in
-    // every phase, so consecutive phases need no barrier between them.
-    int L = 1;
-    while (L < 4 && (int)blockDim.x >= 2 * L * R.part_free_max) L *= 2;
-    const int sub = threadIdx.x & (L - 1), grp = threadIdx.x / L, ngrp = blockDim.x / L;
-    for (;;) {
-        for (int k = grp; k < pt.nfr; k += ngrp) {
-            if (sub != 0) continue;
-            const int i = pt.f0 + k;
-            df u[3];
-            for (int c = 0; c < 3; ++c) {
-                df v = {vh[c * n + i], vl[c * n + i]};
-                const df a = {ah[c * n + i], al[c * n + i]};
-                v = df_add(v, df_mul(hdt, a));
-                u[c] = df_add({uh[c * n + i], ul[c * n + i]}, df_mul(dt, v));
-                vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
-                uh[c * n + i] = u[c].hi; ul[c * n + i] = u[c].lo;
-            }
-            Pl[k] = make_float4(u[0].hi, u[1].hi, u[2].hi, 0.f);
-            Q0[k] = make_float4(u[0].lo, u[1].lo, u[2].lo, 0.f);
-        }
-        cl.sync();
-        float rs = 0.f, kes = 0.f;
-        for (int kb = 0; kb < pt.nfr; kb += ngrp) {
-            const int k = kb + grp;
-            const bool valid = k < pt.nfr;
-            df g[3] = {df_from(0.f), df_from(0.f), df_from(0.f)};
-            if (valid) gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g[0], g[1], g[2], sub, L);
-            df_group_sum(g[0], g[1], g[2], L);
-            if (!valid || sub != 0) continue;
-            const int i = pt.f0 + k;
-            const df im = {imh[i], iml[i]};
-            float vv = 0.f;
-            for (int c = 0; c < 3; ++c) {
-                df v = {vh[c * n + i], vl[c * n + i]};
-                const df a = df_sub(df_mul(g[c], im), df_mul(cdf, v));
-                v = df_add(v, df_mul(hdt, a));
-                ah[c * n + i] = a.hi; al[c * n + i] = a.lo;
-                vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
-                fg[c * n + i] = g[c].hi;
-                rs += g[c].hi * g[c].hi;
-                vv += v.hi * v.hi;
-            }
-            if (want_k) kes += 0.5f * vv / imh[i];
-        }
-        publish(sh, pt, rs, kes, want_k, rb);
-        cl.sync();
-        r2 = cluster_total(sh.red, rb, pt.C);
-        if (want_k) k2 = cluster_total(sh.kred, rb, pt.C);
-        rb = (rb + 1) % kLeadBufs;
-        ++it;
-        if (!isfinite(r2.hi)) { status = RVE_NAN; break; }
-        if (df_le(r2, thresh2)) { status = RVE_OK; break; }
-        if (it >= P.max_iter) { status = RVE_MAXITER; break; }
-        if (P.lead_iters >= 0 ? it >= P.lead_iters : df_le(r2, lead2)) break;
-    }
-    if (pt.me == 0 && threadIdx.x == 0) {
-        O.iters[p] = it;
-        O.lead[p] = it;
-        O.status[p] = status;
-        O.f_ref[p] = f_ref;
-        O.rel_res[p] = df_to_double(r2);  // squared residual, finished by the FP32 kernel
-        O.ke[p] = want_k ? df_to_double(k2) : 0.0;
-    }
-    cl.sync();
-}
-
 // FP32 increment of one element's force on node i from neighbour j about the
 // reference state: t(d_ref + dd) - t(d_ref) + q_ref dd, accumulated into g.
 // p* hold FP32 reference positions, q* the FP32 displacement increments;
@@ -429,6 +276,10 @@ struct Staged {
     int *SD;       // per own free node: row length
     int *EB;       // per own free node: first element of its row
     int *SS;       // per slab + 1: first slot
+    // lead kernel only (K0, K1 then hold the double-float D and L)
+    float4 *KA;    // per element
+    float4 *TA;    // per element
+    float2 *TB;    // per element
 };
 
 // 32-bit shared-memory address of p and its image in cluster CTA `rank`.
@@ -586,6 +437,378 @@ __device__ __forceinline__ Verdict judge(const MixedShared &sh, const Part &pt, 
     v.code = !isfinite(r2.hi) ? RVE_NAN : df_le(r2, thresh2) ? RVE_OK : done >= max_iter ? RVE_MAXITER : -1;
     v.r2h = r2.hi; v.r2l = r2.lo; v.k2h = k2.hi; v.k2l = k2.lo;
     return v;
+}
+
+// ---------------------------------------------------------------------------
+// lead kernel with the element table (STAGE)
+// ---------------------------------------------------------------------------
+// The lead's element table: the same element list and node rows as the FP32
+// kernel's (element_counts, element_offsets), with per element
+//   K0 = (D, L).hi, K1 = (D, L).lo  (D = X_b - X_a, double-float),
+//   KA = ((EA/L).hi, (EA/L).lo, shared::cta address of a's displacement in
+//        buffer 0, address of b's: shared::cta, or shared::cluster with bit 0
+//        set when b lives in another CTA),
+//   TA, TB = the iteration's double-float force on a (hi xyz + lo x; lo yz).
+// Displacements rotate through two buffers (hi then lo arrays per buffer), so
+// one cluster barrier per iteration suffices.
+__device__ void lead_elements(const MixedShared &sh, const DevMesh &M, const RveDesc &R, const Part &pt,
+                              const int32_t *rowptr, const float4 *U0, const Staged &st) {
+    for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+        const int beg = rowptr[pt.f0 + k], deg = st.SD[k];
+        int u = st.EB[k];
+        int slot = st.SS[k >> 5] + (k & 31);
+        for (int e = 0; e < deg; ++e, slot += 32) {
+            const int64_t kk = R.csr0 + beg + e;
+            const int cp = M.col_part[kk];
+            const int r = cp >> 16, loc = cp & 0xffff;
+            if (b_end(r, loc, k, pt)) {
+                const int jb = rowptr[pt.f0 + loc], jd = st.SD[loc];
+                int v = st.EB[loc];
+                for (int x = 0; x < jd; ++x) {
+                    const int cq = M.col_part[R.csr0 + jb + x];
+                    const int rq = cq >> 16, lq = cq & 0xffff;
+                    if (rq == pt.me && lq == k) break;
+                    v += !b_end(rq, lq, loc, pt);
+                }
+                st.NS[slot] = ((uint32_t)v << 1) | 1u;
+                continue;
+            }
+            const float2 eh = M.eaf[kk], el = M.eaf_lo[kk];
+            const df kax = df_mul({eh.x, el.x}, {eh.y, el.y});
+            const uint32_t qb = smem_addr(U0 + loc);
+            const uint32_t ab = r == pt.me ? qb : (cluster_addr(qb, (uint32_t)r) | 1u);
+            st.K0[u] = M.dh[kk];
+            st.K1[u] = M.dl[kk];
+            st.KA[u] = make_float4(kax.hi, kax.lo, __uint_as_float(smem_addr(U0 + k)), __uint_as_float(ab));
+            st.NS[slot] = (uint32_t)u << 1;
+            ++u;
+        }
+    }
+}
+
+__device__ __forceinline__ float4 ld_any(uint32_t a) {
+    return (a & 1u) ? ld_cluster(a & ~1u) : ld_local(a);
+}
+
+// Double-float iterations until the relative residual first drops below
+// lead_tol (or lead_iters), NaN or max_iter. The residual test of evaluation
+// n-2 runs in one judging warp per CTA between the arrive and the wait of
+// iteration n; the others read its verdict after the next barrier, and the
+// hand-over happens at the end of that iteration, so the handed-over state
+// (u, v, a and g_ref of one evaluation) is consistent. The hand-over state's
+// own residual is then totalled by every warp.
+__device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M,
+                                 const DevState &S, const RveDesc &R, const Part &pt,
+                                 const SolveParams &P, float4 *U0, const Staged &st, int part_cap,
+                                 int elem_cap, int slot_cap, const df &lead2, const df &thresh2,
+                                 const df &dt, const df &hdt, const df &cdf, int64_t &it,
+                                 int &status, df &r2, df &k2) {
+    const int n = R.n_nodes, m = pt.m();
+    const int64_t n0 = R.node0, b3 = 3 * n0;
+    const int32_t *rowptr = M.rowptr + R.rp0;
+    float *uh = S.uh + b3, *ul = S.ul + b3, *vh = S.vh + b3, *vl = S.vl + b3;
+    float *ah = S.ah + b3, *al = S.al + b3, *fg = S.fg + b3;
+    const float *imh = M.imh + n0, *iml = M.iml + n0;
+    const bool want_k = P.want_ke != 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool judge_warp = warp == (int)(blockDim.x >> 5) - 1;
+    // buffer t: hi at U0 + 2 t part_cap, lo at U0 + (2 t + 1) part_cap
+    const uint32_t lo_off = (uint32_t)(sizeof(float4) * part_cap), buf_off = 2 * lo_off;
+    // buffer 1 starts as a copy of buffer 0 (the fixed nodes never change)
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        U0[2 * part_cap + k] = U0[k];
+        U0[3 * part_cap + k] = U0[part_cap + k];
+    }
+    element_counts(M, R, pt, rowptr, st);
+    __syncthreads();
+    if (threadIdx.x == 0) element_offsets(sh, pt, st);
+    cl.sync();
+    bool over = false;
+    for (int r = 0; r < pt.C; ++r)
+        over |= *cl.map_shared_rank(&sh.elems, r) > elem_cap || *cl.map_shared_rank(&sh.slots, r) > slot_cap;
+    if (over) {  // sized on the host for every part; all CTAs agree
+        status = RVE_NAN;
+        return;
+    }
+    lead_elements(sh, M, R, pt, rowptr, U0, st);
+    const int n_el = sh.elems;
+    __syncthreads();
+
+    bool vpend = false;
+    for (;;) {
+        const int64_t nidx = it + 1;  // this iteration's evaluation
+        const int t = (int)(nidx & 1), tp = t ^ 1;
+        const int vb = (int)(nidx & 3);
+        {
+            const float4 *Hp = U0 + 2 * tp * part_cap, *Lp = Hp + part_cap;
+            float4 *Hc = U0 + 2 * t * part_cap, *Lc = Hc + part_cap;
+            for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+                const int i = pt.f0 + k;
+                const float4 ph = Hp[k], pl = Lp[k];
+                const float uh0[3] = {ph.x, ph.y, ph.z}, ul0[3] = {pl.x, pl.y, pl.z};
+                df u[3];
+                for (int c = 0; c < 3; ++c) {
+                    df v = {vh[c * n + i], vl[c * n + i]};
+                    const df a = {ah[c * n + i], al[c * n + i]};
+                    v = df_add(v, df_mul(hdt, a));
+                    u[c] = df_add({uh0[c], ul0[c]}, df_mul(dt, v));
+                    vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
+                }
+                Hc[k] = make_float4(u[0].hi, u[1].hi, u[2].hi, 0.f);
+                Lc[k] = make_float4(u[0].lo, u[1].lo, u[2].lo, 0.f);
+            }
+        }
+        const bool judge_now = nidx >= 3;
+        cluster_arrive();
+        if (judge_now && judge_warp) {
+            const Verdict v = judge(sh, pt, (int)((nidx - 2) & 3), 0, lead2, want_k, INT64_MAX);
+            if (lane == 0) sh.vd[vb] = v;
+        }
+        cluster_wait();
+        const int code = vpend ? sh.vd[(nidx - 1) & 3].code : -1;
+        vpend = judge_now;
+        // element forces in displacement form (gather_df's operations)
+        const uint32_t toff = (uint32_t)t * buf_off;
+        for (int u = threadIdx.x; u < n_el; u += blockDim.x) {
+            const float4 Dh = st.K0[u], Dl = st.K1[u], ka = st.KA[u];
+            const uint32_t aa = __float_as_uint(ka.z) + toff, ab = __float_as_uint(ka.w) + toff;
+            const float4 pi = ld_local(aa), qi = ld_local(aa + lo_off);
+            const float4 pj = ld_any(ab), qj = ld_any(ab + lo_off);
+            const df e0 = df_sub({pj.x, qj.x}, {pi.x, qi.x}), e1 = df_sub({pj.y, qj.y}, {pi.y, qi.y}),
+                     e2 = df_sub({pj.z, qj.z}, {pi.z, qi.z});
+            const df D0 = {Dh.x, Dl.x}, D1 = {Dh.y, Dl.y}, D2 = {Dh.z, Dl.z}, L = {Dh.w, Dl.w};
+            const df d0 = df_add(D0, e0), d1 = df_add(D1, e1), d2 = df_add(D2, e2);
+            const df h = df_add(df_add(df_mul(e0, df_add(D0, d0)), df_mul(e1, df_add(D1, d1))),
+                                df_mul(e2, df_add(D2, d2)));
+            const df l2 = df_add(df_sqr(L), h);
+            const df rl = df_rsqrt(l2);
+            const df l = df_mul(l2, rl);
+            const df q = df_mul(df_mul({ka.x, ka.y}, df_mul(h, rl)), df_rcp(df_add(l, L)));
+            const df t0 = df_mul(q, d0), t1 = df_mul(q, d1), t2 = df_mul(q, d2);
+            st.TA[u] = make_float4(t0.hi, t1.hi, t2.hi, t0.lo);
+            st.TB[u] = make_float2(t1.lo, t2.lo);
+        }
+        __syncthreads();
+        // node sums in CSR row order, then acceleration and velocity
+        float rs = 0.f, kes = 0.f;
+        for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+            const int deg = st.SD[k];
+            int sl = st.SS[k >> 5] + (k & 31);
+            df g[3] = {df_from(0.f), df_from(0.f), df_from(0.f)};
+            for (int j = 0; j < deg; ++j, sl += 32) {
+                const uint32_t w = st.NS[sl];
+                const float4 ta = st.TA[w >> 1];
+                const float2 tb = st.TB[w >> 1];
+                df f0 = {ta.x, ta.w}, f1 = {ta.y, tb.x}, f2 = {ta.z, tb.y};
+                if (w & 1u) {
+                    f0 = {-f0.hi, -f0.lo}; f1 = {-f1.hi, -f1.lo}; f2 = {-f2.hi, -f2.lo};
+                }
+                g[0] = df_add(g[0], f0); g[1] = df_add(g[1], f1); g[2] = df_add(g[2], f2);
+            }
+            const int i = pt.f0 + k;
+            const df im = {imh[i], iml[i]};
+            float vv = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                df v = {vh[c * n + i], vl[c * n + i]};
+                const df a = df_sub(df_mul(g[c], im), df_mul(cdf, v));
+                v = df_add(v, df_mul(hdt, a));
+                ah[c * n + i] = a.hi; al[c * n + i] = a.lo;
+                vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
+                fg[c * n + i] = g[c].hi;
+                rs += g[c].hi * g[c].hi;
+                vv += v.hi * v.hi;
+            }
+            if (want_k) kes += 0.5f * vv / imh[i];
+        }
+        for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        if (want_k)
+            for (int o = 16; o > 0; o >>= 1) kes += __shfl_xor_sync(0xffffffffu, kes, o);
+        if (lane == 0) {
+            sh.own[vb][0][warp] = rs;
+            if (want_k) sh.own[vb][1][warp] = kes;
+        }
+        it = nidx;
+        if (code == RVE_NAN) break;
+        if (it >= P.max_iter) break;
+        if (P.lead_iters >= 0 ? it >= P.lead_iters : code == RVE_OK) break;
+    }
+    // the hand-over evaluation's own residual, by every warp
+    cl.sync();
+    const Verdict v = judge(sh, pt, (int)(it & 3), it, thresh2, want_k, P.max_iter);
+    r2 = {v.r2h, v.r2l};
+    k2 = {v.k2h, v.k2l};
+    status = v.code >= 0 ? v.code : RVE_PENDING;
+    // the double-float displacement for the FP32 kernel and the output
+    const int t = (int)(it & 1);
+    const float4 *Hc = U0 + 2 * t * part_cap, *Lc = Hc + part_cap;
+    for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+        const int i = pt.f0 + k;
+        const float4 ph = Hc[k], pl = Lc[k];
+        uh[i] = ph.x; uh[n + i] = ph.y; uh[2 * n + i] = ph.z;
+        ul[i] = pl.x; ul[n + i] = pl.y; ul[2 * n + i] = pl.z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// lead kernel: setup (Algorithm 1 lines up to the loop) and the double-float
+// iterations
+// ---------------------------------------------------------------------------
+template <bool STAGE>
+__device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
+                         const DevResults &O, const SolveParams &P, int p, float4 *Pl, float4 *Q0,
+                         const Staged &st, int part_cap, int elem_cap, int slot_cap, int &rb) {
+    const RveDesc R = M.rve[p];
+    const Part pt = make_part(M, R, p, (int)cl.block_rank(), (int)cl.num_blocks());
+    const int n = R.n_nodes, m = pt.m();
+    const int64_t n0 = R.node0, b3 = 3 * n0;
+    const int32_t *rowptr = M.rowptr + R.rp0;
+    double F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = P.F[9 * (int64_t)p + k];
+    float *uh = S.uh + b3, *ul = S.ul + b3, *vh = S.vh + b3, *vl = S.vl + b3;
+    float *ah = S.ah + b3, *al = S.al + b3, *fg = S.fg + b3;
+    const float *imh = M.imh + n0, *iml = M.iml + n0;
+    const bool want_k = P.want_ke != 0;
+
+    // affine displacement (F - I) X for f_ref, and the initial displacement
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int i = pt.gidx(k);
+        const double X[3] = {M.X0[n0 + i], M.X1[n0 + i], M.X2[n0 + i]};
+        const double *uw[3] = {S.u0 + n0, S.u1 + n0, S.u2 + n0};
+        df ua[3];
+        const bool fixed = k >= pt.nfr;
+        for (int r = 0; r < 3; ++r) {
+            const double xa = dadd(dadd(dmul(F[3 * r], X[0]), dmul(F[3 * r + 1], X[1])), dmul(F[3 * r + 2], X[2]));
+            const double uaff = dsub(xa, X[r]);
+            ua[r] = df_from_double(uaff);
+            double u;
+            if (fixed || P.init == 1) u = uaff;
+            else if (P.init == 2) u = uw[r][i];
+            else u = 0.0;
+            const df ud = df_from_double(u);
+            uh[r * n + i] = ud.hi;
+            ul[r * n + i] = ud.lo;
+        }
+        Pl[k] = make_float4(ua[0].hi, ua[1].hi, ua[2].hi, 0.f);
+        Q0[k] = make_float4(ua[0].lo, ua[1].lo, ua[2].lo, 0.f);
+    }
+    cl.sync();
+    float acc = 0.f;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        df g0, g1, g2;
+        gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g0, g1, g2);
+        acc += g0.hi * g0.hi + g1.hi * g1.hi + g2.hi * g2.hi;
+    }
+    publish(sh, pt, acc, 0.f, false, rb);
+    cl.sync();
+    const double f_aff = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
+    rb = (rb + 1) % kLeadBufs;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int i = pt.gidx(k);
+        Pl[k] = make_float4(uh[i], uh[n + i], uh[2 * n + i], 0.f);
+        Q0[k] = make_float4(ul[i], ul[n + i], ul[2 * n + i], 0.f);
+    }
+    cl.sync();
+    acc = 0.f;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        df g[3];
+        gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g[0], g[1], g[2]);
+        acc += g[0].hi * g[0].hi + g[1].hi * g[1].hi + g[2].hi * g[2].hi;
+        if (k < pt.nfr) {
+            const int i = pt.gidx(k);
+            const df im = {imh[i], iml[i]};
+            for (int r = 0; r < 3; ++r) {
+                const df a = df_mul(g[r], im);
+                ah[r * n + i] = a.hi; al[r * n + i] = a.lo;
+                vh[r * n + i] = 0.f; vl[r * n + i] = 0.f;
+                fg[r * n + i] = g[r].hi;
+            }
+        }
+    }
+    publish(sh, pt, acc, 0.f, false, rb);
+    cl.sync();
+    const double f0 = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
+    rb = (rb + 1) % kLeadBufs;
+    const double f_ref = f_aff > f0 ? f_aff : f0;
+    const df thresh2 = df_from_double(dmul(dmul(P.tol, f_ref), dmul(P.tol, f_ref)));
+    const df lead2 = df_from_double(dmul(dmul(P.lead_tol, f_ref), dmul(P.lead_tol, f_ref)));
+    const double dt64 = dmul(P.alpha, R.dtc);
+    const df dt = df_from_double(dt64), hdt = df_from_double(dmul(0.5, dt64));
+    const df cdf = df_from_double(R.c);
+
+    int64_t it = 0;
+    int status = RVE_PENDING;
+    df r2 = df_from(0.f), k2 = df_from(0.f);
+    if (STAGE) {
+        lead_loop_staged(cl, sh, M, S, R, pt, P, Pl, st, part_cap, elem_cap, slot_cap, lead2, thresh2,
+                         dt, hdt, cdf, it, status, r2, k2);
+    } else {
+    // L lanes share a node's edges; lane 0 of group k owns node k's state in
+    // every phase, so consecutive phases need no barrier between them.
+    int L = 1;
+    while (L < 4 && (int)blockDim.x >= 2 * L * R.part_free_max) L *= 2;
+    const int sub = threadIdx.x & (L - 1), grp = threadIdx.x / L, ngrp = blockDim.x / L;
+    for (;;) {
+        for (int k = grp; k < pt.nfr; k += ngrp) {
+            if (sub != 0) continue;
+            const int i = pt.f0 + k;
+            df u[3];
+            for (int c = 0; c < 3; ++c) {
+                df v = {vh[c * n + i], vl[c * n + i]};
+                const df a = {ah[c * n + i], al[c * n + i]};
+                v = df_add(v, df_mul(hdt, a));
+                u[c] = df_add({uh[c * n + i], ul[c * n + i]}, df_mul(dt, v));
+                vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
+                uh[c * n + i] = u[c].hi; ul[c * n + i] = u[c].lo;
+            }
+            Pl[k] = make_float4(u[0].hi, u[1].hi, u[2].hi, 0.f);
+            Q0[k] = make_float4(u[0].lo, u[1].lo, u[2].lo, 0.f);
+        }
+        cl.sync();
+        float rs = 0.f, kes = 0.f;
+        for (int kb = 0; kb < pt.nfr; kb += ngrp) {
+            const int k = kb + grp;
+            const bool valid = k < pt.nfr;
+            df g[3] = {df_from(0.f), df_from(0.f), df_from(0.f)};
+            if (valid) gather_df(M, R, rowptr, sh, pt, k, Pl, Q0, 0, g[0], g[1], g[2], sub, L);
+            df_group_sum(g[0], g[1], g[2], L);
+            if (!valid || sub != 0) continue;
+            const int i = pt.f0 + k;
+            const df im = {imh[i], iml[i]};
+            float vv = 0.f;
+            for (int c = 0; c < 3; ++c) {
+                df v = {vh[c * n + i], vl[c * n + i]};
+                const df a = df_sub(df_mul(g[c], im), df_mul(cdf, v));
+                v = df_add(v, df_mul(hdt, a));
+                ah[c * n + i] = a.hi; al[c * n + i] = a.lo;
+                vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
+                fg[c * n + i] = g[c].hi;
+                rs += g[c].hi * g[c].hi;
+                vv += v.hi * v.hi;
+            }
+            if (want_k) kes += 0.5f * vv / imh[i];
+        }
+        publish(sh, pt, rs, kes, want_k, rb);
+        cl.sync();
+        r2 = cluster_total(sh.red, rb, pt.C);
+        if (want_k) k2 = cluster_total(sh.kred, rb, pt.C);
+        rb = (rb + 1) % kLeadBufs;
+        ++it;
+        if (!isfinite(r2.hi)) { status = RVE_NAN; break; }
+        if (df_le(r2, thresh2)) { status = RVE_OK; break; }
+        if (it >= P.max_iter) { status = RVE_MAXITER; break; }
+        if (P.lead_iters >= 0 ? it >= P.lead_iters : df_le(r2, lead2)) break;
+    }
+    }
+    if (pt.me == 0 && threadIdx.x == 0) {
+        O.iters[p] = it;
+        O.lead[p] = it;
+        O.status[p] = status;
+        O.f_ref[p] = f_ref;
+        O.rel_res[p] = df_to_double(r2);  // squared residual, finished by the FP32 kernel
+        O.ke[p] = want_k ? df_to_double(k2) : 0.0;
+    }
+    cl.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -975,19 +1198,43 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
 
 }  // namespace
 
-__global__ void __launch_bounds__(512) dr_mixed_lead_kernel(DevMesh M, DevState S, DevResults O,
-                                                            SolveParams P, int part_cap) {
+template <bool STAGE>
+__global__ void __launch_bounds__(512, 1) dr_mixed_lead_kernel(DevMesh M, DevState S, DevResults O,
+                                                            SolveParams P, int part_cap, int free_cap,
+                                                            int elem_cap, int slot_cap) {
     extern __shared__ __align__(16) float4 dsm[];
     __shared__ MixedShared sh;
     cg::cluster_group cl = cg::this_cluster();
     float4 *Pl = dsm, *Q0 = dsm + part_cap;
     float4 *Qb[kBufs] = {Q0, Q0, Q0, Q0};
+    Staged st = {};
+    if (STAGE) {
+        // layout as in mixed_lead_smem: two displacement buffers, then the tables
+        char *base = reinterpret_cast<char *>(dsm + 4 * (size_t)part_cap);
+        st.K0 = reinterpret_cast<float4 *>(base);
+        base += 16 * (size_t)elem_cap;
+        st.K1 = reinterpret_cast<float4 *>(base);
+        base += 16 * (size_t)elem_cap;
+        st.KA = reinterpret_cast<float4 *>(base);
+        base += 16 * (size_t)elem_cap;
+        st.TA = reinterpret_cast<float4 *>(base);
+        base += 16 * (size_t)elem_cap;
+        st.TB = reinterpret_cast<float2 *>(base);
+        base += 8 * (size_t)elem_cap;
+        st.NS = reinterpret_cast<uint32_t *>(base);
+        base += 4 * (size_t)slot_cap;
+        st.SD = reinterpret_cast<int *>(base);
+        base += 4 * (size_t)free_cap;
+        st.EB = reinterpret_cast<int *>(base);
+        base += 4 * (size_t)free_cap;
+        st.SS = reinterpret_cast<int *>(base);
+    }
     map_remote(cl, sh, Pl, Qb, (int)cl.num_blocks());
     int rb = 0;
     for (;;) {
         const int item = next_item(cl, sh, P.counter);
         if (item >= P.queue_len) return;
-        lead_rve(cl, sh, M, S, O, P, P.queue[item], Pl, Q0, rb);
+        lead_rve<STAGE>(cl, sh, M, S, O, P, P.queue[item], Pl, Q0, st, part_cap, elem_cap, slot_cap, rb);
     }
 }
 
@@ -1068,18 +1315,35 @@ size_t mixed_fp32_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, s
     return staged <= limit ? staged : plain;
 }
 
+size_t mixed_lead_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, size_t limit) {
+    const size_t plain = kLeadPlainNodeBytes * (size_t)part_cap;
+    const size_t F = (size_t)free_cap, U = (size_t)elem_cap, S = (size_t)slot_cap;
+    const size_t staged =
+        align16(2 * plain + 4 * 16 * U + 8 * U + 4 * S + 2 * 4 * F + 4 * (F / 32 + 2));
+    return staged <= limit ? staged : plain;
+}
+
+bool mixed_staged(int lead, size_t smem, int part_cap) {
+    return smem > (lead ? kLeadPlainNodeBytes : kFp32NodeBytes) * (size_t)part_cap;
+}
+
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
                     int lead, int clusters, int parts, int block, size_t smem, int part_cap,
                     int free_cap, int elem_cap, int slot_cap, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = mixed_config(clusters, parts, block, smem, attr, st);
+    const bool staged = mixed_staged(lead, smem, part_cap);
     cudaError_t e;
-    if (lead) {
-        prepare(dr_mixed_lead_kernel, smem);
-        e = cudaLaunchKernelEx(&cfg, dr_mixed_lead_kernel, m, s, r, p,
-                               (int)(smem / (2 * sizeof(float4))));
-    } else if (smem > kFp32NodeBytes * (size_t)part_cap) {
+    if (lead && staged) {
+        prepare(dr_mixed_lead_kernel<true>, smem);
+        e = cudaLaunchKernelEx(&cfg, dr_mixed_lead_kernel<true>, m, s, r, p, part_cap, free_cap,
+                               elem_cap, slot_cap);
+    } else if (lead) {
+        prepare(dr_mixed_lead_kernel<false>, smem);
+        e = cudaLaunchKernelEx(&cfg, dr_mixed_lead_kernel<false>, m, s, r, p, part_cap, free_cap,
+                               elem_cap, slot_cap);
+    } else if (staged) {
         prepare(dr_mixed_fp32_kernel<true>, smem);
         e = cudaLaunchKernelEx(&cfg, dr_mixed_fp32_kernel<true>, m, s, r, p, part_cap, free_cap,
                                elem_cap, slot_cap);
@@ -1095,12 +1359,16 @@ int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, co
 int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = mixed_config(parts * 64, parts, block, smem, attr, nullptr);
+    const bool staged = mixed_staged(lead, smem, part_cap);
     int n = 0;
     cudaError_t e;
-    if (lead) {
-        prepare(dr_mixed_lead_kernel, smem);
-        e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_lead_kernel, &cfg);
-    } else if (smem > kFp32NodeBytes * (size_t)part_cap) {
+    if (lead && staged) {
+        prepare(dr_mixed_lead_kernel<true>, smem);
+        e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_lead_kernel<true>, &cfg);
+    } else if (lead) {
+        prepare(dr_mixed_lead_kernel<false>, smem);
+        e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_lead_kernel<false>, &cfg);
+    } else if (staged) {
         prepare(dr_mixed_fp32_kernel<true>, smem);
         e = cudaOccupancyMaxActiveClusters(&n, dr_mixed_fp32_kernel<true>, &cfg);
     } else {

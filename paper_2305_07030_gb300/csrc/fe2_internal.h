@@ -123,6 +123,11 @@ int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r,
 // Dynamic shared memory of the FP32 kernel for a class: the staged node state,
 // plus each part's element table and rows when they fit within `limit` bytes.
 size_t mixed_fp32_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, size_t limit);
+// Dynamic shared memory of the lead kernel for a class: one double-float
+// displacement per node, or two plus the element table when they fit.
+size_t mixed_lead_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, size_t limit);
+// Whether a launch with `smem` bytes uses the shared-memory element table.
+bool mixed_staged(int lead, size_t smem, int part_cap);
 // Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.
 int occupancy_dr_fp64(int smem_positions, int block, size_t smem);
 int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap);

@@ -262,10 +262,8 @@ bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]
 
 // Shared-memory bytes per staged node of the mixed solver's FP32 kernel
 // (reference position and four rotating increment buffers, float4 each;
-// velocity and acceleration, float4 + float2) and of its lead kernel
-// (double-float displacement, two float4).
+// velocity and acceleration, float4 + float2); it bounds the part size.
 constexpr size_t kMixedNodeBytes = 104;
-constexpr size_t kLeadNodeBytes = 32;
 
 // Number of cluster CTAs for an RVE of n nodes in the mixed solver: a power
 // of two with about `target` nodes per CTA, enough parts for the staged state
@@ -730,10 +728,11 @@ fe2_status check_opts(const fe2_opts &o) {
 // warps to hide its latency chain). A fixed default keeps every RVE's result
 // independent of which other RVEs share its launch (partial sums follow the
 // thread mapping).
-int mixed_block(const SizeClass &c, int requested, bool lead) {
-    (void)c;
-    if (requested) return lead ? std::min(requested, 256) : requested;
-    return lead ? 256 : 512;
+// CTA size of a mixed launch: 512 threads, except the lead kernel without its
+// element table (256: two CTAs per SM, its registers allow no more).
+int mixed_block(int requested, bool lead, bool staged) {
+    const int cap = lead && !staged ? 256 : 512;
+    return requested ? std::min(requested, cap) : cap;
 }
 
 // Longest-processing-time order from measured cost: once a solve has
@@ -792,10 +791,10 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
         ++*launches;
     } else {
         for (int lead = 1; lead >= 0; --lead) {
-            const int block = mixed_block(c, o.block_threads, lead != 0);
-            const size_t smem = lead ? kLeadNodeBytes * c.part_max
-                                     : mixed_fp32_smem(c.part_max, c.free_max, c.elem_max, c.slot_max,
-                                                       b->smem_optin - 16384);
+            const size_t limit = b->smem_optin - 16384;
+            const size_t smem = lead ? mixed_lead_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit)
+                                     : mixed_fp32_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit);
+            const int block = mixed_block(o.block_threads, lead != 0, mixed_staged(lead, smem, c.part_max));
             const int resident = occupancy_dr_mixed(lead, c.parts, block, smem, c.part_max);
             if (resident < 1)
                 return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
