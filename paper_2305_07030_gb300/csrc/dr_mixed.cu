@@ -490,6 +490,47 @@ __device__ __forceinline__ float4 ld_any(uint32_t a) {
     return (a & 1u) ? ld_cluster(a & ~1u) : ld_local(a);
 }
 
+// Double-float element force in displacement form (the operations of
+// gather_df) for element u, written to TA/TB.
+__device__ __forceinline__ void lead_element_force(const Staged &st, int u, const float4 &pi,
+                                                   const float4 &qi, const float4 &pj, const float4 &qj) {
+    const float4 Dh = st.K0[u], Dl = st.K1[u];
+    const float2 kax = make_float2(st.KA[u].x, st.KA[u].y);
+    const df e0 = df_sub({pj.x, qj.x}, {pi.x, qi.x}), e1 = df_sub({pj.y, qj.y}, {pi.y, qi.y}),
+             e2 = df_sub({pj.z, qj.z}, {pi.z, qi.z});
+    const df D0 = {Dh.x, Dl.x}, D1 = {Dh.y, Dl.y}, D2 = {Dh.z, Dl.z}, L = {Dh.w, Dl.w};
+    const df d0 = df_add(D0, e0), d1 = df_add(D1, e1), d2 = df_add(D2, e2);
+    const df h = df_add(df_add(df_mul(e0, df_add(D0, d0)), df_mul(e1, df_add(D1, d1))),
+                        df_mul(e2, df_add(D2, d2)));
+    const df l2 = df_add(df_sqr(L), h);
+    const df rl = df_rsqrt(l2);
+    const df l = df_mul(l2, rl);
+    const df q = df_mul(df_mul({kax.x, kax.y}, df_mul(h, rl)), df_rcp(df_add(l, L)));
+    const df t0 = df_mul(q, d0), t1 = df_mul(q, d1), t2 = df_mul(q, d2);
+    st.TA[u] = make_float4(t0.hi, t1.hi, t2.hi, t0.lo);
+    st.TB[u] = make_float2(t1.lo, t2.lo);
+}
+
+// Elements ua and ub (ub < 0: none) of displacement buffer offset toff: all
+// loads first, then the two independent chains.
+__device__ __forceinline__ void lead_element_pair(const Staged &st, int ua, int ub, uint32_t toff,
+                                                  uint32_t lo_off) {
+    const float4 ka = st.KA[ua];
+    const uint32_t a0 = __float_as_uint(ka.z) + toff, a1 = __float_as_uint(ka.w) + toff;
+    const float4 pi = ld_local(a0), qi = ld_local(a0 + lo_off);
+    const float4 pj = ld_any(a1), qj = ld_any(a1 + lo_off);
+    if (ub >= 0) {
+        const float4 kb = st.KA[ub];
+        const uint32_t b0 = __float_as_uint(kb.z) + toff, b1 = __float_as_uint(kb.w) + toff;
+        const float4 pi2 = ld_local(b0), qi2 = ld_local(b0 + lo_off);
+        const float4 pj2 = ld_any(b1), qj2 = ld_any(b1 + lo_off);
+        lead_element_force(st, ua, pi, qi, pj, qj);
+        lead_element_force(st, ub, pi2, qi2, pj2, qj2);
+    } else {
+        lead_element_force(st, ua, pi, qi, pj, qj);
+    }
+}
+
 // Double-float iterations until the relative residual first drops below
 // lead_tol (or lead_iters), NaN or max_iter. The residual test of evaluation
 // n-2 runs in one judging warp per CTA between the arrive and the wait of
@@ -567,26 +608,12 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
         cluster_wait();
         const int code = vpend ? sh.vd[(nidx - 1) & 3].code : -1;
         vpend = judge_now;
-        // element forces in displacement form (gather_df's operations)
+        // element forces in displacement form (gather_df's operations), two
+        // elements per thread in flight
         const uint32_t toff = (uint32_t)t * buf_off;
-        for (int u = threadIdx.x; u < n_el; u += blockDim.x) {
-            const float4 Dh = st.K0[u], Dl = st.K1[u], ka = st.KA[u];
-            const uint32_t aa = __float_as_uint(ka.z) + toff, ab = __float_as_uint(ka.w) + toff;
-            const float4 pi = ld_local(aa), qi = ld_local(aa + lo_off);
-            const float4 pj = ld_any(ab), qj = ld_any(ab + lo_off);
-            const df e0 = df_sub({pj.x, qj.x}, {pi.x, qi.x}), e1 = df_sub({pj.y, qj.y}, {pi.y, qi.y}),
-                     e2 = df_sub({pj.z, qj.z}, {pi.z, qi.z});
-            const df D0 = {Dh.x, Dl.x}, D1 = {Dh.y, Dl.y}, D2 = {Dh.z, Dl.z}, L = {Dh.w, Dl.w};
-            const df d0 = df_add(D0, e0), d1 = df_add(D1, e1), d2 = df_add(D2, e2);
-            const df h = df_add(df_add(df_mul(e0, df_add(D0, d0)), df_mul(e1, df_add(D1, d1))),
-                                df_mul(e2, df_add(D2, d2)));
-            const df l2 = df_add(df_sqr(L), h);
-            const df rl = df_rsqrt(l2);
-            const df l = df_mul(l2, rl);
-            const df q = df_mul(df_mul({ka.x, ka.y}, df_mul(h, rl)), df_rcp(df_add(l, L)));
-            const df t0 = df_mul(q, d0), t1 = df_mul(q, d1), t2 = df_mul(q, d2);
-            st.TA[u] = make_float4(t0.hi, t1.hi, t2.hi, t0.lo);
-            st.TB[u] = make_float2(t1.lo, t2.lo);
+        const int step = blockDim.x;
+        for (int u0 = threadIdx.x; u0 < n_el; u0 += 2 * step) {
+            lead_element_pair(st, u0, u0 + step < n_el ? u0 + step : -1, toff, lo_off);
         }
         __syncthreads();
         // node sums in CSR row order, then acceleration and velocity
