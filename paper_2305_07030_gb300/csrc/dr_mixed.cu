@@ -280,6 +280,9 @@ struct Staged {
     float4 *KA;    // per element
     float4 *TA;    // per element
     float2 *TB;    // per element
+    float4 *VH;    // per own free node: (v.hi, a.hi x)
+    float4 *VL;    // per own free node: (v.lo, a.lo x)
+    float4 *AY;    // per own free node: (a.hi y, a.hi z, a.lo y, a.lo z)
 };
 
 // 32-bit shared-memory address of p and its image in cluster CTA `rank`.
@@ -573,6 +576,14 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
     }
     lead_elements(sh, M, R, pt, rowptr, U0, st);
     const int n_el = sh.elems;
+    // velocity and acceleration of the own free nodes live in shared memory
+    // during the loop (owner thread k in every phase)
+    for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
+        const int i = pt.f0 + k;
+        st.VH[k] = make_float4(vh[i], vh[n + i], vh[2 * n + i], ah[i]);
+        st.VL[k] = make_float4(vl[i], vl[n + i], vl[2 * n + i], al[i]);
+        st.AY[k] = make_float4(ah[n + i], ah[2 * n + i], al[n + i], al[2 * n + i]);
+    }
     __syncthreads();
 
     bool vpend = false;
@@ -584,17 +595,18 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
             const float4 *Hp = U0 + 2 * tp * part_cap, *Lp = Hp + part_cap;
             float4 *Hc = U0 + 2 * t * part_cap, *Lc = Hc + part_cap;
             for (int k = threadIdx.x; k < pt.nfr; k += blockDim.x) {
-                const int i = pt.f0 + k;
                 const float4 ph = Hp[k], pl = Lp[k];
+                const float4 vhk = st.VH[k], vlk = st.VL[k], ay = st.AY[k];
                 const float uh0[3] = {ph.x, ph.y, ph.z}, ul0[3] = {pl.x, pl.y, pl.z};
-                df u[3];
+                const float v_h[3] = {vhk.x, vhk.y, vhk.z}, v_l[3] = {vlk.x, vlk.y, vlk.z};
+                const float a_h[3] = {vhk.w, ay.x, ay.y}, a_l[3] = {vlk.w, ay.z, ay.w};
+                df u[3], v[3];
                 for (int c = 0; c < 3; ++c) {
-                    df v = {vh[c * n + i], vl[c * n + i]};
-                    const df a = {ah[c * n + i], al[c * n + i]};
-                    v = df_add(v, df_mul(hdt, a));
-                    u[c] = df_add({uh0[c], ul0[c]}, df_mul(dt, v));
-                    vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
+                    v[c] = df_add({v_h[c], v_l[c]}, df_mul(hdt, {a_h[c], a_l[c]}));
+                    u[c] = df_add({uh0[c], ul0[c]}, df_mul(dt, v[c]));
                 }
+                st.VH[k] = make_float4(v[0].hi, v[1].hi, v[2].hi, vhk.w);
+                st.VL[k] = make_float4(v[0].lo, v[1].lo, v[2].lo, vlk.w);
                 Hc[k] = make_float4(u[0].hi, u[1].hi, u[2].hi, 0.f);
                 Lc[k] = make_float4(u[0].lo, u[1].lo, u[2].lo, 0.f);
             }
@@ -634,17 +646,21 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
             }
             const int i = pt.f0 + k;
             const df im = {imh[i], iml[i]};
+            const float4 vhk = st.VH[k], vlk = st.VL[k];
+            const float v_h[3] = {vhk.x, vhk.y, vhk.z}, v_l[3] = {vlk.x, vlk.y, vlk.z};
             float vv = 0.f;
+            df v[3], a[3];
             for (int c = 0; c < 3; ++c) {
-                df v = {vh[c * n + i], vl[c * n + i]};
-                const df a = df_sub(df_mul(g[c], im), df_mul(cdf, v));
-                v = df_add(v, df_mul(hdt, a));
-                ah[c * n + i] = a.hi; al[c * n + i] = a.lo;
-                vh[c * n + i] = v.hi; vl[c * n + i] = v.lo;
+                v[c] = {v_h[c], v_l[c]};
+                a[c] = df_sub(df_mul(g[c], im), df_mul(cdf, v[c]));
+                v[c] = df_add(v[c], df_mul(hdt, a[c]));
                 fg[c * n + i] = g[c].hi;
                 rs += g[c].hi * g[c].hi;
-                vv += v.hi * v.hi;
+                vv += v[c].hi * v[c].hi;
             }
+            st.VH[k] = make_float4(v[0].hi, v[1].hi, v[2].hi, a[0].hi);
+            st.VL[k] = make_float4(v[0].lo, v[1].lo, v[2].lo, a[0].lo);
+            st.AY[k] = make_float4(a[1].hi, a[2].hi, a[1].lo, a[2].lo);
             if (want_k) kes += 0.5f * vv / imh[i];
         }
         for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
@@ -673,6 +689,11 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
         const float4 ph = Hc[k], pl = Lc[k];
         uh[i] = ph.x; uh[n + i] = ph.y; uh[2 * n + i] = ph.z;
         ul[i] = pl.x; ul[n + i] = pl.y; ul[2 * n + i] = pl.z;
+        const float4 vhk = st.VH[k], vlk = st.VL[k], ay = st.AY[k];
+        vh[i] = vhk.x; vh[n + i] = vhk.y; vh[2 * n + i] = vhk.z;
+        vl[i] = vlk.x; vl[n + i] = vlk.y; vl[2 * n + i] = vlk.z;
+        ah[i] = vhk.w; ah[n + i] = ay.x; ah[2 * n + i] = ay.y;
+        al[i] = vlk.w; al[n + i] = ay.z; al[2 * n + i] = ay.w;
     }
 }
 
@@ -1236,8 +1257,12 @@ __global__ void __launch_bounds__(512, 1) dr_mixed_lead_kernel(DevMesh M, DevSta
     float4 *Qb[kBufs] = {Q0, Q0, Q0, Q0};
     Staged st = {};
     if (STAGE) {
-        // layout as in mixed_lead_smem: two displacement buffers, then the tables
-        char *base = reinterpret_cast<char *>(dsm + 4 * (size_t)part_cap);
+        // layout as in mixed_lead_smem: two displacement buffers, velocity and
+        // acceleration, then the tables
+        st.VH = dsm + 4 * (size_t)part_cap;
+        st.VL = st.VH + free_cap;
+        st.AY = st.VL + free_cap;
+        char *base = reinterpret_cast<char *>(st.AY + free_cap);
         st.K0 = reinterpret_cast<float4 *>(base);
         base += 16 * (size_t)elem_cap;
         st.K1 = reinterpret_cast<float4 *>(base);
@@ -1346,7 +1371,7 @@ size_t mixed_lead_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, s
     const size_t plain = kLeadPlainNodeBytes * (size_t)part_cap;
     const size_t F = (size_t)free_cap, U = (size_t)elem_cap, S = (size_t)slot_cap;
     const size_t staged =
-        align16(2 * plain + 4 * 16 * U + 8 * U + 4 * S + 2 * 4 * F + 4 * (F / 32 + 2));
+        align16(2 * plain + 3 * 16 * F + 4 * 16 * U + 8 * U + 4 * S + 2 * 4 * F + 4 * (F / 32 + 2));
     return staged <= limit ? staged : plain;
 }
 
