@@ -862,6 +862,18 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
 // ---------------------------------------------------------------------------
 // FP32 kernel: increment iterations, reference refreshes, final state, stress
 // ---------------------------------------------------------------------------
+// The next iteration's partial velocity update (Algorithm 1: v += dt/2 a)
+// and displacement increment (u += dt v, as an increment on top of d) for one
+// node, from its velocity w and acceleration a after this iteration.
+__device__ __forceinline__ void next_increment(float w0, float w1, float w2, float a0, float a1, float a2,
+                                               const float4 &d, float hdtf, float dtf, float4 &sv,
+                                               float2 &sa, float4 &next) {
+    const float v0 = w0 + hdtf * a0, v1 = w1 + hdtf * a1, v2 = w2 + hdtf * a2;
+    sv = make_float4(v0, v1, v2, a0);
+    sa = make_float2(a1, a2);
+    next = make_float4(d.x + dtf * v0, d.y + dtf * v1, d.z + dtf * v2, 0.f);
+}
+
 template <bool STAGE>
 __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
                          const DevResults &O, const SolveParams &P, int p, float4 *Pl,
@@ -951,25 +963,21 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         int since = 0;
         const int32_t *colp = M.col_part + R.csr0;
         const float2 *eafp = M.eaf + R.csr0;
-        int b = 0, bp = kBufs - 1;  // buffers of evaluation nidx and nidx - 1
-        for (int64_t nidx = first; status == RVE_PENDING; ++nidx, bp = b, b = (b + 1 == kBufs ? 0 : b + 1)) {
-            // partial velocity update; displacement increment into buffer b
-            {
-                const float4 *prev = Qb[bp];
-                float4 *cur = Qb[b];
-                for (int k = grp; k < pt.nfr; k += ngrp) {
-                    if (sub != 0) continue;
-                    float4 va = SV[k];
-                    const float2 a12 = SA[k];
-                    const float w0 = va.x + hdtf * va.w;
-                    const float w1 = va.y + hdtf * a12.x;
-                    const float w2 = va.z + hdtf * a12.y;
-                    va.x = w0; va.y = w1; va.z = w2;
-                    SV[k] = va;
-                    const float4 d = nidx == first ? make_float4(0.f, 0.f, 0.f, 0.f) : prev[k];
-                    cur[k] = make_float4(d.x + dtf * w0, d.y + dtf * w1, d.z + dtf * w2, 0.f);
-                }
-            }
+        // Partial velocity update and displacement increment of the first
+        // iteration; every later one is done by the node's owner right after
+        // the node's velocity update of the previous iteration (the values are
+        // still in registers), so an iteration begins at the barrier.
+        for (int k = grp; k < pt.nfr; k += ngrp) {
+            if (sub != 0) continue;
+            const float4 va = SV[k];
+            const float2 a12 = SA[k];
+            next_increment(va.x, va.y, va.z, va.w, a12.x, a12.y, make_float4(0.f, 0.f, 0.f, 0.f),
+                           hdtf, dtf, SV[k], SA[k], Qb[0][k]);
+        }
+        int b = 0;  // buffer of evaluation nidx
+        for (int64_t nidx = first; status == RVE_PENDING; ++nidx, b = (b + 1 == kBufs ? 0 : b + 1)) {
+            const int bn = b + 1 == kBufs ? 0 : b + 1;  // buffer of evaluation nidx + 1
+            const int bp = b == 0 ? kBufs - 1 : b - 1;  // buffer of evaluation nidx - 1
             const bool rebase = since >= K;
             cluster_arrive();
             // Residual test of evaluation nidx-2 while the barrier completes: by
@@ -1063,8 +1071,7 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     const float a0 = g0 * im - cf * va.x, a1 = g1 * im - cf * va.y,
                                 a2 = g2 * im - cf * va.z;
                     const float w0 = va.x + hdtf * a0, w1 = va.y + hdtf * a1, w2 = va.z + hdtf * a2;
-                    SV[k] = make_float4(w0, w1, w2, a0);
-                    SA[k] = make_float2(a1, a2);
+                    next_increment(w0, w1, w2, a0, a1, a2, cur[k], hdtf, dtf, SV[k], SA[k], Qb[bn][k]);
                     rs += g0 * g0 + g1 * g1 + g2 * g2;
                     if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
                 }
@@ -1104,8 +1111,7 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                         const float a1 = g1 * im - cf * w1;
                         const float a2 = g2 * im - cf * w2;
                         w0 += hdtf * a0; w1 += hdtf * a1; w2 += hdtf * a2;
-                        SV[k] = make_float4(w0, w1, w2, a0);
-                        SA[k] = make_float2(a1, a2);
+                        next_increment(w0, w1, w2, a0, a1, a2, cur[k], hdtf, dtf, SV[k], SA[k], Qb[bn][k]);
                         rs += g0 * g0 + g1 * g1 + g2 * g2;
                         if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
                     }
@@ -1158,8 +1164,8 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                             const float a1 = g1 * im - cf * w1;
                             const float a2 = g2 * im - cf * w2;
                             w0 += hdtf * a0; w1 += hdtf * a1; w2 += hdtf * a2;
-                            SV[k] = make_float4(w0, w1, w2, a0);
-                            SA[k] = make_float2(a1, a2);
+                            next_increment(w0, w1, w2, a0, a1, a2, cur[k], hdtf, dtf, SV[k], SA[k],
+                                           Qb[bn][k]);
                             rs += g0 * g0 + g1 * g1 + g2 * g2;
                             if (want_k) kes += 0.5f * (w0 * w0 + w1 * w1 + w2 * w2) / im;
                         }
