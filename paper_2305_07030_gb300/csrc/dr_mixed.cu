@@ -31,11 +31,21 @@
 //    and across warps and CTAs in double-float; the threshold (tol f_ref)^2 is
 //    formed in FP64 once per RVE; the stress sum is FP64.
 //
-// Synchronisation of the FP32 kernel. Three increment buffers rotate, so one
-// cluster barrier per iteration suffices and the residual reduction of
-// iteration n-2 runs between the barrier's arrive and wait of iteration n,
-// hidden behind the barrier latency; its state (buffer (n-2) mod 3) is still
-// intact when the test succeeds.
+// Synchronisation of the FP32 kernel. One cluster barrier per iteration.
+// Five displacement-increment buffers rotate. Each node's owner thread
+// computes the next iteration's increment right after the node's velocity
+// update, so an iteration begins at the barrier. Between the barrier's arrive
+// and wait, every warp publishes its residual partial of the previous
+// evaluation to its own CTA, and one warp per CTA totals evaluation n-3 across
+// the cluster (DSMEM reads) and leaves a verdict. All warps read the verdict
+// after the next barrier. If the test succeeded, they finish with the state of
+// the tested evaluation, whose buffer is still intact.
+//
+// The element forces of the FP32 kernel and of the lead come from a
+// shared-memory element table. Each element with an end among a CTA's free
+// nodes is evaluated once per iteration, spread evenly over the threads. Each
+// node then sums the +- results of its CSR row in row order. The two ends see
+// exactly opposite values, so this equals the per-direction evaluation.
 #include <cooperative_groups.h>
 
 #include "df64.cuh"
@@ -49,8 +59,8 @@ namespace {
 
 constexpr int kMaxWarps = 16;  // blocks of at most 512 threads
 constexpr int kLeadBufs = 3;   // lead kernel: rotating partial buffers
-constexpr int kBufs = 4;       // FP32 kernel: rotating increment / partial buffers
-// FP32 kernel shared memory per staged node: reference position, four
+constexpr int kBufs = 5;       // FP32 kernel: rotating increment / partial buffers
+// FP32 kernel shared memory per staged node: reference position, five
 // increment buffers (float4 each), velocity + a.x (float4), a.yz (float2).
 constexpr size_t kFp32NodeBytes = (1 + kBufs + 1) * sizeof(float4) + sizeof(float2);
 // Lead kernel shared memory per node without the element table: one
@@ -975,20 +985,34 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                            hdtf, dtf, SV[k], SA[k], Qb[0][k]);
         }
         int b = 0;  // buffer of evaluation nidx
+        float part_rs = 0.f, part_ke = 0.f;  // this thread's partials of evaluation nidx-1
+        int part_b = -1;                     // and their buffer (-1: none yet)
         for (int64_t nidx = first; status == RVE_PENDING; ++nidx, b = (b + 1 == kBufs ? 0 : b + 1)) {
             const int bn = b + 1 == kBufs ? 0 : b + 1;  // buffer of evaluation nidx + 1
             const int bp = b == 0 ? kBufs - 1 : b - 1;  // buffer of evaluation nidx - 1
             const bool rebase = since >= K;
             cluster_arrive();
-            // Residual test of evaluation nidx-2 while the barrier completes: by
-            // one warp per CTA, whose verdict the others read after the next
-            // barrier (buffers rotate through four, so the state of the tested
-            // evaluation is intact until then); by every warp before a rebase.
+            // While the barrier completes: the per-warp residual partials of
+            // evaluation nidx-1 go to this CTA's buffer, and evaluation nidx-3
+            // (whose partials every CTA has published one barrier ago) is
+            // tested by one warp per CTA, whose verdict the others read after
+            // the next barrier; before a rebase by every warp. Buffers rotate
+            // through five, so the state of a tested evaluation is intact
+            // until its verdict is read.
+            if (part_b >= 0) {
+                for (int o = 16; o > 0; o >>= 1) part_rs += __shfl_xor_sync(0xffffffffu, part_rs, o);
+                if (want_k)
+                    for (int o = 16; o > 0; o >>= 1) part_ke += __shfl_xor_sync(0xffffffffu, part_ke, o);
+                if (lane == 0) {
+                    sh.own[part_b][0][warp] = part_rs;
+                    if (want_k) sh.own[part_b][1][warp] = part_ke;
+                }
+            }
             bool tnow = false;
             int64_t teval = 0;
             int tbuf = 0;
             Verdict mine = {-1, 0.f, 0.f, 0.f, 0.f};
-            if (chk <= nidx - 2) {
+            if (chk <= nidx - 3) {
                 if (rebase || judge_warp) mine = judge(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
                 if (!rebase && judge_warp && lane == 0) sh.vd[b] = mine;
                 tnow = true; teval = chk; tbuf = chkb;
@@ -1005,9 +1029,16 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             }
             vpend = false;
             if (stopv.code < 0 && rebase) {
+                // the reference moves: every earlier evaluation is tested first
                 if (tnow && mine.code >= 0) { stopv = mine; seval = teval; sbuf = tbuf; }
-                else if (chk == nidx - 1) {
-                    // the reference moves: every earlier evaluation is tested first
+                if (stopv.code < 0 && chk == nidx - 2) {  // published one barrier ago
+                    mine = judge(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
+                    if (mine.code >= 0) { stopv = mine; seval = chk; sbuf = chkb; }
+                    ++chk;
+                    chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
+                }
+                if (stopv.code < 0 && chk == nidx - 1) {  // published in this barrier's window
+                    cl.sync();
                     mine = judge(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
                     if (mine.code >= 0) { stopv = mine; seval = chk; sbuf = chkb; }
                     ++chk;
@@ -1172,14 +1203,10 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     }
                 }
             }
-            // this evaluation's per-warp partials, in this CTA's own buffer b
-            for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-            if (want_k)
-                for (int o = 16; o > 0; o >>= 1) kes += __shfl_xor_sync(0xffffffffu, kes, o);
-            if (lane == 0) {
-                sh.own[b][0][warp] = rs;
-                if (want_k) sh.own[b][1][warp] = kes;
-            }
+            // this evaluation's partials are published in the next barrier's window
+            part_rs = rs;
+            part_ke = kes;
+            part_b = b;
             ++since;
         }
     }
@@ -1260,7 +1287,8 @@ __global__ void __launch_bounds__(512, 1) dr_mixed_lead_kernel(DevMesh M, DevSta
     __shared__ MixedShared sh;
     cg::cluster_group cl = cg::this_cluster();
     float4 *Pl = dsm, *Q0 = dsm + part_cap;
-    float4 *Qb[kBufs] = {Q0, Q0, Q0, Q0};
+    float4 *Qb[kBufs];
+    for (int b = 0; b < kBufs; ++b) Qb[b] = Q0;
     Staged st = {};
     if (STAGE) {
         // layout as in mixed_lead_smem: two displacement buffers, velocity and

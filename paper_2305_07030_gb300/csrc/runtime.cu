@@ -261,9 +261,9 @@ namespace {
 bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
 // Shared-memory bytes per staged node of the mixed solver's FP32 kernel
-// (reference position and four rotating increment buffers, float4 each;
+// (reference position and five rotating increment buffers, float4 each;
 // velocity and acceleration, float4 + float2); it bounds the part size.
-constexpr size_t kMixedNodeBytes = 104;
+constexpr size_t kMixedNodeBytes = 120;
 
 // Number of cluster CTAs for an RVE of n nodes in the mixed solver: a power
 // of two with about `target` nodes per CTA, enough parts for the staged state

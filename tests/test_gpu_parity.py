@@ -96,13 +96,14 @@ def test_mixed_within_tolerance_or_rounding_envelope():
 def test_mixed_unstaged_fallback(monkeypatch):
     """Parts too large for the FP32 kernel's shared-memory element table run
     the fallback that re-reads the CSR rows every iteration: with the
-    node-per-CTA target raised, a 2000-node and a 700-node RVE each run in a
-    single CTA, and their size class's tables do not fit."""
+    node-per-CTA target raised, a 2000-node RVE runs as two parts of 1000
+    nodes, whose size class's tables do not fit (a 700-node RVE, one part,
+    runs staged beside it)."""
     monkeypatch.setenv("FE2_NODES_PER_CTA", "8192")
     w = _workload([2000, 700], seed=20)
     env = envelope_batch(w)
     with Batch(w.nets, damping=w.damping) as b:
-        assert list(b.parts()) == [1, 1]
+        assert list(b.parts()) == [2, 1]
         b.solve(w.F, precision="mixed", tol=1e-8)
         out = b.stress()
         u = b.displacement()
