@@ -82,7 +82,7 @@ struct MixedShared {
     float kred[kLeadBufs][kMaxParts * kMaxWarps]; // kinetic-energy partials
     // FP32 kernel: this CTA's per-warp partials (residual, kinetic energy)
     float own[kBufs][2][kMaxWarps];
-    Verdict vd[kBufs];                        // verdicts of the judging warp
+    Verdict vd[kBufs];                        // verdicts of the testing warp
     float *ownp[kMaxParts];                   // every CTA's own
     double sig[kMaxParts][9];                 // stress partials, read by rank 0
     double wsum[kMaxWarps][9];                // per-warp stress partials
@@ -432,7 +432,7 @@ __device__ void element_setup(const MixedShared &sh, const DevMesh &M, const Rve
 // Convergence verdict on one evaluation: the double-float total of every
 // CTA's per-warp partials (fixed order: rank, then warp), read through
 // distributed shared memory.
-__device__ __forceinline__ Verdict judge(const MixedShared &sh, const Part &pt, int buf, int64_t done,
+__device__ __forceinline__ Verdict residual_verdict(const MixedShared &sh, const Part &pt, int buf, int64_t done,
                                          const df &thresh2, bool want_k, int64_t max_iter) {
     const int nw = (int)(blockDim.x >> 5), total = pt.C * nw, lane = threadIdx.x & 31;
     df r2 = df_from(0.f), k2 = df_from(0.f);
@@ -546,7 +546,7 @@ __device__ __forceinline__ void lead_element_pair(const Staged &st, int ua, int 
 
 // Double-float iterations until the relative residual first drops below
 // lead_tol (or lead_iters), NaN or max_iter. The residual test of evaluation
-// n-2 runs in one judging warp per CTA between the arrive and the wait of
+// n-2 runs in one testing warp per CTA between the arrive and the wait of
 // iteration n; the others read its verdict after the next barrier, and the
 // hand-over happens at the end of that iteration, so the handed-over state
 // (u, v, a and g_ref of one evaluation) is consistent. The hand-over state's
@@ -565,7 +565,7 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
     const float *imh = M.imh + n0, *iml = M.iml + n0;
     const bool want_k = P.want_ke != 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool judge_warp = warp == (int)(blockDim.x >> 5) - 1;
+    const bool test_warp = warp == (int)(blockDim.x >> 5) - 1;
     // buffer t: hi at U0 + 2 t part_cap, lo at U0 + (2 t + 1) part_cap
     const uint32_t lo_off = (uint32_t)(sizeof(float4) * part_cap), buf_off = 2 * lo_off;
     // buffer 1 starts as a copy of buffer 0 (the fixed nodes never change)
@@ -621,15 +621,15 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
                 Lc[k] = make_float4(u[0].lo, u[1].lo, u[2].lo, 0.f);
             }
         }
-        const bool judge_now = nidx >= 3;
+        const bool test_now = nidx >= 3;
         cluster_arrive();
-        if (judge_now && judge_warp) {
-            const Verdict v = judge(sh, pt, (int)((nidx - 2) & 3), 0, lead2, want_k, INT64_MAX);
+        if (test_now && test_warp) {
+            const Verdict v = residual_verdict(sh, pt, (int)((nidx - 2) & 3), 0, lead2, want_k, INT64_MAX);
             if (lane == 0) sh.vd[vb] = v;
         }
         cluster_wait();
         const int code = vpend ? sh.vd[(nidx - 1) & 3].code : -1;
-        vpend = judge_now;
+        vpend = test_now;
         // element forces in displacement form (gather_df's operations), two
         // elements per thread in flight
         const uint32_t toff = (uint32_t)t * buf_off;
@@ -687,7 +687,7 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
     }
     // the hand-over evaluation's own residual, by every warp
     cl.sync();
-    const Verdict v = judge(sh, pt, (int)(it & 3), it, thresh2, want_k, P.max_iter);
+    const Verdict v = residual_verdict(sh, pt, (int)(it & 3), it, thresh2, want_k, P.max_iter);
     r2 = {v.r2h, v.r2l};
     k2 = {v.k2h, v.k2l};
     status = v.code >= 0 ? v.code : RVE_PENDING;
@@ -926,7 +926,7 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         const int L = lanes;
         const int sub = threadIdx.x & (L - 1), grp = threadIdx.x / L, ngrp = blockDim.x / L;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const bool judge_warp = warp == (int)(blockDim.x >> 5) - 1;
+        const bool test_warp = warp == (int)(blockDim.x >> 5) - 1;
         // x_ref = X + u (FP32 rounding of the double-float sum), increments zero;
         // g_ref = fg from the lead's last force evaluation at exactly this state
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
@@ -966,7 +966,7 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         const int64_t first = it;  // evaluation index of the first FP32 iteration
         int64_t chk = first;       // next evaluation whose residual is still untested
         int chkb = 0;              // its buffer
-        // the verdict the judging warp wrote in the previous iteration
+        // the verdict the testing warp wrote in the previous iteration
         bool vpend = false;
         int64_t veval = 0;
         int vbuf = 0;
@@ -1013,8 +1013,8 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             int tbuf = 0;
             Verdict mine = {-1, 0.f, 0.f, 0.f, 0.f};
             if (chk <= nidx - 3) {
-                if (rebase || judge_warp) mine = judge(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
-                if (!rebase && judge_warp && lane == 0) sh.vd[b] = mine;
+                if (rebase || test_warp) mine = residual_verdict(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
+                if (!rebase && test_warp && lane == 0) sh.vd[b] = mine;
                 tnow = true; teval = chk; tbuf = chkb;
                 ++chk;
                 chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
@@ -1032,14 +1032,14 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                 // the reference moves: every earlier evaluation is tested first
                 if (tnow && mine.code >= 0) { stopv = mine; seval = teval; sbuf = tbuf; }
                 if (stopv.code < 0 && chk == nidx - 2) {  // published one barrier ago
-                    mine = judge(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
+                    mine = residual_verdict(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
                     if (mine.code >= 0) { stopv = mine; seval = chk; sbuf = chkb; }
                     ++chk;
                     chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
                 }
                 if (stopv.code < 0 && chk == nidx - 1) {  // published in this barrier's window
                     cl.sync();
-                    mine = judge(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
+                    mine = residual_verdict(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
                     if (mine.code >= 0) { stopv = mine; seval = chk; sbuf = chkb; }
                     ++chk;
                     chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
