@@ -97,6 +97,18 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# DRAM bytes (read + write) of one dr_mixed_fp32_kernel launch, scaled from
+# one ncu capture of the same kernel: a 5000-node RVE of the 64 x 5000
+# workload for 30,000 iterations read 1,940,224 B and wrote 5,888 B. The
+# traffic is each RVE's data and state read once; it does not grow with
+# iterations, so a launch's traffic scales with its number of RVEs.
+FP32_DRAM_BYTES_PER_RVE = 1_940_224 + 5_888
+
+
+def fp32_dram_traffic(n_rve):
+    return float(FP32_DRAM_BYTES_PER_RVE * n_rve)
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2305_07030_gb300 as fe2
@@ -218,7 +230,8 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": 9 * 8 * P, "d2h_bytes_per_step": (9 * 8 + 8 + 8 + 4) * P},
         "gpu_launches": launches,
         "roofline": {"bound": "smem", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s",
-                     "frac": achieved / smem_gbs, "traffic": None,
+                     "frac": achieved / smem_gbs,
+                     "traffic": fp32_dram_traffic(P) if args.precision == "mixed" else None,
                      "kernel": kname, "kernel_ms": kms, "lead_kernel_ms": lead_ms,
                      "lead_iters_mean": float(np.mean(leads)),
                      "peak_source": "measured live: fe2_probe_smem_bandwidth (float4 shared-memory "
