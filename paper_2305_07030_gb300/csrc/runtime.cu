@@ -373,14 +373,7 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     if (E > 0 && (!conn || !EA)) return fail(FE2_EINVAL, "NULL conn or EA");
     if (2 * E >= ((int64_t)1 << 31)) return fail(FE2_EINVAL, "too many elements in one batch");
 
-    int dev = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    cudaDeviceProp prop;
-    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
-    if (prop.major != 10 || prop.minor != 3)
-        return fail(FE2_ENODEV, std::string("need an sm_103 GPU, found ") + prop.name);
-
-    // ---- validation ----
+    // ---- validation (host only, before any device call) ----
     for (int64_t i = 0; i < N; ++i)
         if (!finite3(X + 3 * i)) return fail(FE2_EINVAL, "non-finite coordinate at node " + std::to_string(i));
     for (int32_t p = 0; p < n_rve; ++p) {
@@ -406,6 +399,13 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
             return fail(FE2_EINVAL, "RVE " + std::to_string(p) + " repeats an element");
     }
+
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(FE2_ENODEV, std::string("need an sm_103 GPU, found ") + prop.name);
 
     fe2_batch *b = new fe2_batch();
     b->n_rve = n_rve;
