@@ -130,6 +130,39 @@ fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, const double
                             void *stream, fe2_batch **out);
 
 /*
+ * Inspection call, host only (no device is touched): the packing that
+ * fe2_batch_create computes for the same inputs (Algorithm 1: compute the
+ * mesh connectivity array; Section III: the free/fixed reordering and the
+ * packed CRS-style layout of many RVEs). It is the one call whose outputs
+ * show the internal node order.
+ *
+ * Inputs as for fe2_batch_create. smem_optin is the device's opt-in shared
+ * memory per block in bytes (it bounds the part size); nodes_per_cta is the
+ * part-size target (<= 0: the default, as in fe2_batch_create).
+ * Outputs (HOST, caller-allocated; each may be NULL):
+ * parts     n_rve: CTAs (spatial parts) per RVE, a power of two <= 16.
+ * perm      N: for each internal (permuted) node, the caller's global node
+ *           index. Each RVE keeps its node range; within it, free nodes come
+ *           first, part by part, then the fixed ones, part by part.
+ * rowptr    N + n_rve: per RVE p, n_p + 1 CSR row offsets starting at
+ *           node_off[p] + p, relative to the RVE's first entry.
+ * col       2*E: per CSR entry, the neighbour's internal RVE-local index.
+ *           Entries of a row follow the caller's neighbour ids.
+ * col_part  2*E: the same neighbour as (part << 16 | index within its part).
+ * part_off  n_rve * 34: per RVE, the first internal free node of each part
+ *           (17 offsets), then the first fixed node of each part counted from
+ *           the RVE's first fixed node (17 offsets).
+ *
+ * Returns FE2_EINVAL for the inputs fe2_batch_create rejects, or for
+ * smem_optin <= 16384.
+ */
+fe2_status fe2_batch_layout(int32_t n_rve, const int64_t *node_off, const double *X,
+                            const int64_t *elem_off, const int32_t *conn, const double *EA,
+                            const uint8_t *fixed, int64_t smem_optin, int32_t nodes_per_cta,
+                            int32_t *parts, int64_t *perm, int32_t *rowptr, int32_t *col,
+                            int32_t *col_part, int32_t *part_off);
+
+/*
  * Solve every RVE of the batch for its deformation gradient (Algorithm 1,
  * loop to convergence), asynchronously on `stream`.
  *

@@ -59,6 +59,7 @@ def _load():
     lib.fe2_batch_poll.argtypes = [P, I32, P, P, P, P, P, P]
     lib.fe2_serve.argtypes = [P, I32, P, P, P, C.POINTER(Opts), C.POINTER(Opts), I32, D, P, P, P, P]
     lib.fe2_batch_parts.argtypes = [P, P]
+    lib.fe2_batch_layout.argtypes = [I32, P, P, P, P, P, P, I64, I32, P, P, P, P, P, P]
     lib.fe2_probe_smem_bandwidth.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.restype = C.c_int
     lib.fe2_rve_solve_noalloc.argtypes = [I32, I32, P, P, P, P, P, D, D, C.POINTER(Opts), P, P, P,
@@ -75,7 +76,7 @@ def _load():
                  "fe2_batch_get_displacement", "fe2_batch_set_displacement",
                  "fe2_batch_destroy", "fe2_batch_info", "fe2_batch_kernel_times",
                  "fe2_batch_diagnostics", "fe2_batch_parts", "fe2_batch_submit",
-                 "fe2_batch_poll", "fe2_serve"):
+                 "fe2_batch_poll", "fe2_serve", "fe2_batch_layout"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -149,6 +150,34 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def layout(nets, smem_optin=232448, nodes_per_cta=0):
+    """The internal packing that ``Batch(nets)`` would use, computed on the
+    host without a device (``fe2_batch_layout``): parts per RVE, the node
+    permutation, CSR rows and columns, and part offsets."""
+    n_rve = len(nets)
+    node_off = np.zeros(n_rve + 1, np.int64)
+    elem_off = np.zeros(n_rve + 1, np.int64)
+    for p, net in enumerate(nets):
+        node_off[p + 1] = node_off[p] + net.X.shape[0]
+        elem_off[p + 1] = elem_off[p] + net.elems.shape[0]
+    X = np.ascontiguousarray(np.concatenate([n.X for n in nets]), np.float64)
+    conn = np.ascontiguousarray(np.concatenate([n.elems for n in nets]), np.int32)
+    EA = np.ascontiguousarray(np.concatenate([n.EA for n in nets]), np.float64)
+    fixed = np.ascontiguousarray(np.concatenate([n.fixed for n in nets]), np.uint8)
+    N, E = int(node_off[-1]), int(elem_off[-1])
+    out = {"parts": np.zeros(n_rve, np.int32), "perm": np.zeros(N, np.int64),
+           "rowptr": np.zeros(N + n_rve, np.int32), "col": np.zeros(2 * E, np.int32),
+           "col_part": np.zeros(2 * E, np.int32), "part_off": np.zeros(n_rve * 34, np.int32)}
+    _check(_lib.fe2_batch_layout(n_rve, _ptr(node_off), _ptr(X), _ptr(elem_off), _ptr(conn),
+                                 _ptr(EA), _ptr(fixed), int(smem_optin), int(nodes_per_cta),
+                                 _ptr(out["parts"]), _ptr(out["perm"]), _ptr(out["rowptr"]),
+                                 _ptr(out["col"]), _ptr(out["col_part"]), _ptr(out["part_off"])))
+    out["node_off"] = node_off
+    out["elem_off"] = elem_off
+    out["part_off"] = out["part_off"].reshape(n_rve, 2, 17)
+    return out
 
 
 class Batch:

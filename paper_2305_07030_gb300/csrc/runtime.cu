@@ -352,14 +352,10 @@ void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
     }
 }
 
-}  // namespace
-
-extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, const double *X,
-                                       const int64_t *elem_off, const int32_t *conn,
-                                       const double *EA, const uint8_t *fixed, const double *V0,
-                                       const double *damping, void *stream, fe2_batch **out) {
-    if (!out) return fail(FE2_EINVAL, "out is NULL");
-    *out = nullptr;
+// Input validation of fe2_batch_create and fe2_batch_layout (host only).
+fe2_status validate_batch(int32_t n_rve, const int64_t *node_off, const double *X,
+                          const int64_t *elem_off, const int32_t *conn, const double *EA,
+                          const uint8_t *fixed, const double *V0, const double *damping) {
     if (n_rve < 1) return fail(FE2_EINVAL, "n_rve must be >= 1");
     if (!node_off || !X || !elem_off || !fixed) return fail(FE2_EINVAL, "NULL input array");
     if (node_off[0] != 0 || elem_off[0] != 0) return fail(FE2_EINVAL, "offsets must start at 0");
@@ -373,7 +369,6 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     if (E > 0 && (!conn || !EA)) return fail(FE2_EINVAL, "NULL conn or EA");
     if (2 * E >= ((int64_t)1 << 31)) return fail(FE2_EINVAL, "too many elements in one batch");
 
-    // ---- validation (host only, before any device call) ----
     for (int64_t i = 0; i < N; ++i)
         if (!finite3(X + 3 * i)) return fail(FE2_EINVAL, "non-finite coordinate at node " + std::to_string(i));
     for (int32_t p = 0; p < n_rve; ++p) {
@@ -399,35 +394,46 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
             return fail(FE2_EINVAL, "RVE " + std::to_string(p) + " repeats an element");
     }
+    return FE2_OK;
+}
 
-    int dev = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    cudaDeviceProp prop;
-    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
-    if (prop.major != 10 || prop.minor != 3)
-        return fail(FE2_ENODEV, std::string("need an sm_103 GPU, found ") + prop.name);
+// Host-side packing of a validated batch: per RVE its parts (recursive
+// coordinate bisection) and node permutation (free nodes part by part, then
+// fixed nodes), its CSR rows in permuted order with the neighbour as both an
+// RVE-local id and (part, index in part), and the element list; plus the
+// per-RVE descriptors without device offsets filled in later.
+struct HostLayout {
+    std::vector<RveDesc> rve;
+    std::vector<int64_t> perm_to_orig;   // permuted global -> caller global node
+    std::vector<int32_t> part_free_max;  // per RVE, most free nodes in one part
+    std::vector<double> X, EAcsr, ElEA;  // X as SoA [3][N]
+    std::vector<int32_t> col, colp, Ela, Elb, row, part;
+    std::vector<int64_t> ElemOf, Ga, Gb;
+};
 
-    fe2_batch *b = new fe2_batch();
-    b->n_rve = n_rve;
-    b->n_nodes = N;
-    b->n_elems = E;
-    b->n_csr = 2 * E;
-    b->device = dev;
-    b->sm_count = prop.multiProcessorCount;
-    b->smem_optin = prop.sharedMemPerBlockOptin;
-    b->rve.resize(n_rve);
-    b->perm_to_orig.resize(N);
-    b->part_free_max.resize(n_rve);
-    const int target = std::max(64, env_int("FE2_NODES_PER_CTA", 1024));
-    const size_t smem_cap = b->smem_optin - 16384;
-
-    // ---- packing: parts, permutation, CSR rows, element list ----
-    std::vector<double> hX(3 * N);
-    std::vector<double> hEAcsr(2 * E), hElEA(E);
-    std::vector<int32_t> hcol(2 * E), hcolp(2 * E), hEla(E), hElb(E);
-    std::vector<int64_t> hElemOf(2 * E), hGa(E), hGb(E);
-    std::vector<int32_t> hrow((size_t)N + n_rve);
-    std::vector<int32_t> hpart((size_t)n_rve * 2 * (kMaxParts + 1), 0);
+void build_layout(int32_t n_rve, const int64_t *node_off, const double *X, const int64_t *elem_off,
+                  const int32_t *conn, const double *EA, const uint8_t *fixed, const double *V0,
+                  const double *damping, int target, size_t smem_cap, HostLayout &L) {
+    const int64_t N = node_off[n_rve], E = elem_off[n_rve];
+    L.rve.assign(n_rve, RveDesc{});
+    L.perm_to_orig.assign(N, 0);
+    L.part_free_max.assign(n_rve, 0);
+    L.X.assign(3 * N, 0.0);
+    L.EAcsr.assign(2 * E, 0.0);
+    L.ElEA.assign(E, 0.0);
+    L.col.assign(2 * E, 0);
+    L.colp.assign(2 * E, 0);
+    L.Ela.assign(E, 0);
+    L.Elb.assign(E, 0);
+    L.ElemOf.assign(2 * E, 0);
+    L.Ga.assign(E, 0);
+    L.Gb.assign(E, 0);
+    L.row.assign((size_t)N + n_rve, 0);
+    L.part.assign((size_t)n_rve * 2 * (kMaxParts + 1), 0);
+    std::vector<double> &hX = L.X, &hEAcsr = L.EAcsr, &hElEA = L.ElEA;
+    std::vector<int32_t> &hcol = L.col, &hcolp = L.colp, &hEla = L.Ela, &hElb = L.Elb, &hrow = L.row,
+                         &hpart = L.part;
+    std::vector<int64_t> &hElemOf = L.ElemOf, &hGa = L.Ga, &hGb = L.Gb;
     int64_t csr_pos = 0;
     for (int32_t p = 0; p < n_rve; ++p) {
         const int64_t base = node_off[p];
@@ -489,7 +495,7 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
             rows[a].push_back({c, e});
             rows[c].push_back({a, e});
         }
-        RveDesc &R = b->rve[p];
+        RveDesc &R = L.rve[p];
         R.node0 = base;
         R.rp0 = base + p;
         R.csr0 = csr_pos;
@@ -527,11 +533,11 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         }
         R.part_elem_max = elem_max;
         R.part_slot_max = slot_max;
-        b->part_free_max[p] = free_max;
+        L.part_free_max[p] = free_max;
         int32_t pos = 0;
         for (int k = 0; k < n; ++k) {
             const int orig = order[k];
-            b->perm_to_orig[base + k] = base + orig;
+            L.perm_to_orig[base + k] = base + orig;
             for (int r = 0; r < 3; ++r) hX[r * N + base + k] = X[3 * (base + orig) + r];
             auto &row = rows[orig];
             std::sort(row.begin(), row.end());
@@ -555,6 +561,54 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
             hElEA[e] = EA[e];
         }
     }
+
+}
+
+}  // namespace
+
+extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, const double *X,
+                                       const int64_t *elem_off, const int32_t *conn,
+                                       const double *EA, const uint8_t *fixed, const double *V0,
+                                       const double *damping, void *stream, fe2_batch **out) {
+    if (!out) return fail(FE2_EINVAL, "out is NULL");
+    *out = nullptr;
+    {
+        const fe2_status v = validate_batch(n_rve, node_off, X, elem_off, conn, EA, fixed, V0, damping);
+        if (v != FE2_OK) return v;
+    }
+    const int64_t N = node_off[n_rve], E = elem_off[n_rve];
+
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(FE2_ENODEV, std::string("need an sm_103 GPU, found ") + prop.name);
+
+    fe2_batch *b = new fe2_batch();
+    b->n_rve = n_rve;
+    b->n_nodes = N;
+    b->n_elems = E;
+    b->n_csr = 2 * E;
+    b->device = dev;
+    b->sm_count = prop.multiProcessorCount;
+    b->smem_optin = prop.sharedMemPerBlockOptin;
+    b->rve.resize(n_rve);
+    b->perm_to_orig.resize(N);
+    b->part_free_max.resize(n_rve);
+    const int target = std::max(64, env_int("FE2_NODES_PER_CTA", 1024));
+    const size_t smem_cap = b->smem_optin - 16384;
+
+    // ---- packing: parts, permutation, CSR rows, element list ----
+    HostLayout L;
+    build_layout(n_rve, node_off, X, elem_off, conn, EA, fixed, V0, damping, target, smem_cap, L);
+    b->rve = L.rve;
+    b->perm_to_orig = L.perm_to_orig;
+    b->part_free_max = L.part_free_max;
+    std::vector<double> &hX = L.X, &hEAcsr = L.EAcsr, &hElEA = L.ElEA;
+    std::vector<int32_t> &hcol = L.col, &hcolp = L.colp, &hEla = L.Ela, &hElb = L.Elb, &hrow = L.row,
+                         &hpart = L.part;
+    std::vector<int64_t> &hElemOf = L.ElemOf, &hGa = L.Ga, &hGb = L.Gb;
 
     // ---- device allocation and upload ----
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -705,6 +759,29 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         return rc;
     }
     *out = b;
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_layout(int32_t n_rve, const int64_t *node_off, const double *X,
+                                       const int64_t *elem_off, const int32_t *conn,
+                                       const double *EA, const uint8_t *fixed, int64_t smem_optin,
+                                       int32_t nodes_per_cta, int32_t *parts, int64_t *perm,
+                                       int32_t *rowptr, int32_t *col, int32_t *col_part,
+                                       int32_t *part_off) {
+    const fe2_status v = validate_batch(n_rve, node_off, X, elem_off, conn, EA, fixed, nullptr, nullptr);
+    if (v != FE2_OK) return v;
+    if (smem_optin <= 16384) return fail(FE2_EINVAL, "smem_optin must exceed 16384 bytes");
+    const int target = std::max(64, nodes_per_cta > 0 ? nodes_per_cta : env_int("FE2_NODES_PER_CTA", 1024));
+    HostLayout L;
+    build_layout(n_rve, node_off, X, elem_off, conn, EA, fixed, nullptr, nullptr, target,
+                 (size_t)smem_optin - 16384, L);
+    if (parts)
+        for (int32_t p = 0; p < n_rve; ++p) parts[p] = L.rve[p].n_parts;
+    if (perm) std::copy(L.perm_to_orig.begin(), L.perm_to_orig.end(), perm);
+    if (rowptr) std::copy(L.row.begin(), L.row.end(), rowptr);
+    if (col) std::copy(L.col.begin(), L.col.end(), col);
+    if (col_part) std::copy(L.colp.begin(), L.colp.end(), col_part);
+    if (part_off) std::copy(L.part.begin(), L.part.end(), part_off);
     return FE2_OK;
 }
 

@@ -1,0 +1,115 @@
+"""The host-side packing of fe2_batch_create, read back through the host-only
+fe2_batch_layout (no GPU needed), against its documented invariants:
+
+- parts per RVE follow the cluster-size rule;
+- the node permutation keeps each RVE's range, puts free nodes first part by
+  part (degree order inside a part) and then fixed nodes part by part;
+- RCB parts have equal sizes to within one node;
+- every CSR row lists exactly the node's neighbours, in the caller's
+  neighbour order, so each element appears twice, once from each end;
+- (part, index) of every entry matches the permuted neighbour id.
+"""
+import numpy as np
+import pytest
+
+import rve_inputs as ri
+
+SMEM_OPTIN = 232448       # GB300 opt-in shared memory per block
+NODE_BYTES = 120          # FP32 kernel bytes per staged node (bounds the part size)
+
+
+def _expected_parts(n, target, smem_optin=SMEM_OPTIN):
+    cap = smem_optin - 16384
+    C = 1
+    while C < 16 and (-(-n // C) > target or NODE_BYTES * (-(-n // C) + 64) > cap):
+        C *= 2
+    return C
+
+
+def _check(nets, target, L):
+    node_off, elem_off = L["node_off"], L["elem_off"]
+    for p, net in enumerate(nets):
+        base, n = int(node_off[p]), net.n_nodes
+        C = int(L["parts"][p])
+        assert C == _expected_parts(n, target), (p, n, C)
+        adj = [[] for _ in range(n)]
+        for a, b in net.elems:
+            adj[a].append(b)
+            adj[b].append(a)
+        deg = np.array([len(x) for x in adj])
+        free = (net.fixed == 0) & (deg > 0)
+        nfree = int(free.sum())
+        perm = L["perm"][base:base + n] - base
+        assert sorted(perm.tolist()) == list(range(n))
+        assert free[perm[:nfree]].all() and not free[perm[nfree:]].any()
+        inv = np.empty(n, np.int64)
+        inv[perm] = np.arange(n)
+        pf, pg = L["part_off"][p, 0], L["part_off"][p, 1]
+        assert pf[0] == 0 and pf[C] == nfree and (np.diff(pf[:C + 1]) >= 0).all()
+        assert (pf[C:] == nfree).all()
+        assert pg[0] == 0 and pg[C] == n - nfree and (pg[C:] == n - nfree).all()
+        sizes = [(pf[r + 1] - pf[r]) + (pg[r + 1] - pg[r]) for r in range(C)]
+        assert max(sizes) - min(sizes) <= 1, sizes
+        owner, local = np.empty(n, np.int64), np.empty(n, np.int64)
+        for r in range(C):
+            fr = perm[pf[r]:pf[r + 1]]  # free nodes of part r, caller ids
+            key = [(-deg[i], i) for i in fr]
+            assert key == sorted(key), "free nodes of a part not in degree order"
+            fx = perm[nfree + pg[r]:nfree + pg[r + 1]]
+            assert list(fx) == sorted(fx), "fixed nodes of a part not in id order"
+            owner[fr] = r
+            local[fr] = np.arange(len(fr))
+            owner[fx] = r
+            local[fx] = len(fr) + np.arange(len(fx))
+        rp = L["rowptr"][base + p:base + p + n + 1]
+        csr0 = 2 * int(elem_off[p])
+        assert rp[0] == 0 and rp[-1] == 2 * len(net.elems)
+        for k in range(n):
+            i = perm[k]
+            cols = L["col"][csr0 + rp[k]:csr0 + rp[k + 1]]
+            nb = perm[cols]  # back to caller ids
+            assert list(nb) == sorted(adj[i]), (p, k)
+            cp = L["col_part"][csr0 + rp[k]:csr0 + rp[k + 1]]
+            assert list(cp >> 16) == list(owner[nb]) and list(cp & 0xFFFF) == list(local[nb])
+
+
+def _nets(sizes, seed):
+    rng = np.random.default_rng(seed)
+    return [ri.random_network(int(n), rng) for n in sizes]
+
+
+@pytest.mark.parametrize("target", [0, 256, 1024])
+def test_uneven_batch(target):
+    nets = _nets([37, 300, 777, 2100, 5000], seed=31)
+    import paper_2305_07030_gb300 as m
+    L = m.layout(nets, nodes_per_cta=target)
+    _check(nets, target or 1024, L)
+
+
+def test_isolated_node_is_held_fixed():
+    import paper_2305_07030_gb300 as m
+    rng = np.random.default_rng(32)
+    base = ri.random_network(80, rng)
+    X = np.vstack([base.X, [[0.5, 0.5, 0.5]]])
+    iso = ri.Network(X=X, elems=base.elems, EA=base.EA,
+                     fixed=np.append(base.fixed, 0).astype(np.uint8))
+    L = m.layout([iso])
+    _check([iso], 1024, L)
+    # the isolated node sits among the fixed nodes
+    nfree = int(L["part_off"][0, 0, 1])
+    assert 80 in L["perm"][nfree:].tolist()
+
+
+def test_smem_bounds_the_part_size():
+    """A small shared-memory budget forces more parts than the node target."""
+    import paper_2305_07030_gb300 as m
+    nets = _nets([3000], seed=33)
+    small = 16384 + NODE_BYTES * (800 + 64)
+    L = m.layout(nets, smem_optin=small, nodes_per_cta=4096)
+    assert int(L["parts"][0]) == _expected_parts(3000, 4096, small) == 4
+
+
+def test_rejects_tiny_shared_memory():
+    import paper_2305_07030_gb300 as m
+    with pytest.raises(m.FE2Error, match="smem_optin"):
+        m.layout(_nets([50], seed=34), smem_optin=4096)
