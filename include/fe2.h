@@ -163,6 +163,34 @@ fe2_status fe2_batch_layout(int32_t n_rve, const int64_t *node_off, const double
                             int32_t *col_part, int32_t *part_off);
 
 /*
+ * Inspection call, host only: the launch plan of the mixed solver
+ * (FE2_PREC_MIXED) for these inputs, with the default CTA size. RVEs are
+ * grouped into classes by cluster size; each class runs two persistent
+ * launches (Algorithm 1's loop: the double-float lead, then the FP32 phase).
+ *
+ * Inputs as for fe2_batch_layout. Outputs (HOST, caller-allocated; each may
+ * be NULL); classes beyond max_classes are counted but not written:
+ * n_classes    number of classes.
+ * rve_class    n_rve: each RVE's class (index into the arrays below).
+ * class_parts  per class: CTAs per cluster.
+ * class_rves   per class: number of RVEs.
+ * smem         2 per class: dynamic shared memory per CTA in bytes, for the
+ *              lead kernel then for the FP32 kernel.
+ * staged       2 per class (same order): 1 if that kernel keeps its
+ *              element table in shared memory, 0 if it re-reads the CSR rows
+ *              from global memory every iteration.
+ * block        2 per class (same order): threads per CTA.
+ *
+ * Returns FE2_EINVAL for the inputs fe2_batch_layout rejects.
+ */
+fe2_status fe2_batch_plan(int32_t n_rve, const int64_t *node_off, const double *X,
+                          const int64_t *elem_off, const int32_t *conn, const double *EA,
+                          const uint8_t *fixed, int64_t smem_optin, int32_t nodes_per_cta,
+                          int32_t max_classes, int32_t *n_classes, int32_t *rve_class,
+                          int32_t *class_parts, int32_t *class_rves, int64_t *smem,
+                          int32_t *staged, int32_t *block);
+
+/*
  * Solve every RVE of the batch for its deformation gradient (Algorithm 1,
  * loop to convergence), asynchronously on `stream`.
  *

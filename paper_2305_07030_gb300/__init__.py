@@ -60,6 +60,7 @@ def _load():
     lib.fe2_serve.argtypes = [P, I32, P, P, P, C.POINTER(Opts), C.POINTER(Opts), I32, D, P, P, P, P]
     lib.fe2_batch_parts.argtypes = [P, P]
     lib.fe2_batch_layout.argtypes = [I32, P, P, P, P, P, P, I64, I32, P, P, P, P, P, P]
+    lib.fe2_batch_plan.argtypes = [I32, P, P, P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P]
     lib.fe2_probe_smem_bandwidth.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.restype = C.c_int
     lib.fe2_rve_solve_noalloc.argtypes = [I32, I32, P, P, P, P, P, D, D, C.POINTER(Opts), P, P, P,
@@ -76,7 +77,7 @@ def _load():
                  "fe2_batch_get_displacement", "fe2_batch_set_displacement",
                  "fe2_batch_destroy", "fe2_batch_info", "fe2_batch_kernel_times",
                  "fe2_batch_diagnostics", "fe2_batch_parts", "fe2_batch_submit",
-                 "fe2_batch_poll", "fe2_serve", "fe2_batch_layout"):
+                 "fe2_batch_poll", "fe2_serve", "fe2_batch_layout", "fe2_batch_plan"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -177,6 +178,45 @@ def layout(nets, smem_optin=232448, nodes_per_cta=0):
     out["node_off"] = node_off
     out["elem_off"] = elem_off
     out["part_off"] = out["part_off"].reshape(n_rve, 2, 17)
+    return out
+
+
+def _pack_inputs(nets):
+    n_rve = len(nets)
+    node_off = np.zeros(n_rve + 1, np.int64)
+    elem_off = np.zeros(n_rve + 1, np.int64)
+    for p, net in enumerate(nets):
+        node_off[p + 1] = node_off[p] + net.X.shape[0]
+        elem_off[p + 1] = elem_off[p] + net.elems.shape[0]
+    X = np.ascontiguousarray(np.concatenate([n.X for n in nets]), np.float64)
+    conn = np.ascontiguousarray(np.concatenate([n.elems for n in nets]), np.int32)
+    EA = np.ascontiguousarray(np.concatenate([n.EA for n in nets]), np.float64)
+    fixed = np.ascontiguousarray(np.concatenate([n.fixed for n in nets]), np.uint8)
+    return node_off, X, elem_off, conn, EA, fixed
+
+
+def plan(nets, smem_optin=232448, nodes_per_cta=0):
+    """The mixed solver's launch plan for ``Batch(nets)``, computed on the host
+    without a device (``fe2_batch_plan``): per RVE its class; per class the
+    cluster size, RVE count, and per kernel (lead, FP32) the shared memory per
+    CTA, whether the element table is staged in it, and the CTA size."""
+    n_rve = len(nets)
+    node_off, X, elem_off, conn, EA, fixed = _pack_inputs(nets)
+    m = 8
+    ncls = C.c_int32()
+    out = {"rve_class": np.zeros(n_rve, np.int32), "parts": np.zeros(m, np.int32),
+           "rves": np.zeros(m, np.int32), "smem": np.zeros(2 * m, np.int64),
+           "staged": np.zeros(2 * m, np.int32), "block": np.zeros(2 * m, np.int32)}
+    _check(_lib.fe2_batch_plan(n_rve, _ptr(node_off), _ptr(X), _ptr(elem_off), _ptr(conn), _ptr(EA),
+                               _ptr(fixed), int(smem_optin), int(nodes_per_cta), m, C.byref(ncls),
+                               _ptr(out["rve_class"]), _ptr(out["parts"]), _ptr(out["rves"]),
+                               _ptr(out["smem"]), _ptr(out["staged"]), _ptr(out["block"])))
+    k = ncls.value
+    out["n_classes"] = k
+    for key in ("parts", "rves"):
+        out[key] = out[key][:k]
+    for key in ("smem", "staged", "block"):
+        out[key] = out[key][:2 * k].reshape(k, 2)  # columns: lead, FP32
     return out
 
 

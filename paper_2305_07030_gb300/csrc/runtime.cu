@@ -305,21 +305,22 @@ void rcb(std::vector<int> ids, int parts, const double *X, int64_t base,
 // Bucket RVEs into launch classes. FP64: by staged footprint (24 B/node), so
 // small RVEs are not limited by the occupancy of the largest; RVEs too big for
 // shared memory stage in L2 scratch. Mixed: by cluster size.
-void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
+void build_classes(const std::vector<RveDesc> &rve, const std::vector<int32_t> &part_free_max,
+                   size_t smem_optin, int precision, std::vector<SizeClass> &out) {
     out.clear();
-    std::vector<int32_t> order(b->n_rve);
+    std::vector<int32_t> order(rve.size());
     std::iota(order.begin(), order.end(), 0);
     // longest-processing-time first: largest RVEs lead the queue
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-        return b->rve[x].n_free > b->rve[y].n_free;
+        return rve[x].n_free > rve[y].n_free;
     });
-    const size_t cap = b->smem_optin - 16384;  // room for static shared memory
+    const size_t cap = smem_optin - 16384;  // room for static shared memory
     if (precision == FE2_PREC_FP64) {
         const size_t bounds[] = {16u << 10, 32u << 10, 56u << 10, 112u << 10, cap};
         std::vector<SizeClass> cls(6);
         cls[5].smem_positions = 0;
         for (int32_t p : order) {
-            const size_t need = (size_t)24 * b->rve[p].n_nodes;
+            const size_t need = (size_t)24 * rve[p].n_nodes;
             int c = 5;
             for (int k = 0; k < 5; ++k)
                 if (need <= bounds[k] && need <= cap) { c = k; break; }
@@ -333,13 +334,13 @@ void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
         for (int k = 0; k < 5; ++k) cls[k].parts = 1 << k;
         for (int32_t p : order) {
             int k = 0;
-            while ((1 << k) < b->rve[p].n_parts) ++k;
+            while ((1 << k) < rve[p].n_parts) ++k;
             SizeClass &c = cls[k];
             c.rves.push_back(p);
-            c.part_max = std::max(c.part_max, b->rve[p].part_max);
-            c.free_max = std::max(c.free_max, b->part_free_max[p]);
-            c.elem_max = std::max(c.elem_max, b->rve[p].part_elem_max);
-            c.slot_max = std::max(c.slot_max, b->rve[p].part_slot_max);
+            c.part_max = std::max(c.part_max, rve[p].part_max);
+            c.free_max = std::max(c.free_max, part_free_max[p]);
+            c.elem_max = std::max(c.elem_max, rve[p].part_elem_max);
+            c.slot_max = std::max(c.slot_max, rve[p].part_slot_max);
             c.smem_bytes = kMixedNodeBytes * c.part_max;
         }
         for (auto &c : cls)
@@ -352,7 +353,9 @@ void build_classes(fe2_batch *b, int precision, std::vector<SizeClass> &out) {
     }
 }
 
-// Input validation of fe2_batch_create and fe2_batch_layout (host only).
+int mixed_block(int requested, bool lead, bool staged);
+
+// Input validation of fe2_batch_create and the inspection calls (host only).
 fe2_status validate_batch(int32_t n_rve, const int64_t *node_off, const double *X,
                           const int64_t *elem_off, const int32_t *conn, const double *EA,
                           const uint8_t *fixed, const double *V0, const double *damping) {
@@ -697,8 +700,8 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     if (rc == FE2_OK) A(cudaStreamSynchronize(st), "create sync");
     d_elemof.release(); d_ga.release(); d_gb.release();
     if (rc == FE2_OK) {
-        build_classes(b, FE2_PREC_FP64, b->classes_fp64);
-        build_classes(b, FE2_PREC_MIXED, b->classes_mixed);
+        build_classes(b->rve, b->part_free_max, b->smem_optin, FE2_PREC_FP64, b->classes_fp64);
+        build_classes(b->rve, b->part_free_max, b->smem_optin, FE2_PREC_MIXED, b->classes_mixed);
         // work queues: per class, RVE ids in scheduling order (FP64, then mixed)
         std::vector<int32_t> q(2 * (size_t)n_rve);
         for (auto &c : b->classes_fp64) std::copy(c.rves.begin(), c.rves.end(), q.begin() + c.queue_off);
@@ -782,6 +785,43 @@ extern "C" fe2_status fe2_batch_layout(int32_t n_rve, const int64_t *node_off, c
     if (col) std::copy(L.col.begin(), L.col.end(), col);
     if (col_part) std::copy(L.colp.begin(), L.colp.end(), col_part);
     if (part_off) std::copy(L.part.begin(), L.part.end(), part_off);
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_plan(int32_t n_rve, const int64_t *node_off, const double *X,
+                                     const int64_t *elem_off, const int32_t *conn, const double *EA,
+                                     const uint8_t *fixed, int64_t smem_optin, int32_t nodes_per_cta,
+                                     int32_t max_classes, int32_t *n_classes, int32_t *rve_class,
+                                     int32_t *class_parts, int32_t *class_rves, int64_t *smem,
+                                     int32_t *staged, int32_t *block) {
+    const fe2_status v = validate_batch(n_rve, node_off, X, elem_off, conn, EA, fixed, nullptr, nullptr);
+    if (v != FE2_OK) return v;
+    if (smem_optin <= 16384) return fail(FE2_EINVAL, "smem_optin must exceed 16384 bytes");
+    const int target = std::max(64, nodes_per_cta > 0 ? nodes_per_cta : env_int("FE2_NODES_PER_CTA", 1024));
+    HostLayout L;
+    build_layout(n_rve, node_off, X, elem_off, conn, EA, fixed, nullptr, nullptr, target,
+                 (size_t)smem_optin - 16384, L);
+    std::vector<SizeClass> cls;
+    build_classes(L.rve, L.part_free_max, (size_t)smem_optin, FE2_PREC_MIXED, cls);
+    if (n_classes) *n_classes = (int32_t)cls.size();
+    const size_t limit = (size_t)smem_optin - 16384;  // as in launch_class
+    for (size_t k = 0; k < cls.size(); ++k) {
+        const SizeClass &c = cls[k];
+        if (rve_class)
+            for (int32_t p : c.rves) rve_class[p] = (int32_t)k;
+        if ((int32_t)k >= max_classes) continue;
+        if (class_parts) class_parts[k] = c.parts;
+        if (class_rves) class_rves[k] = (int32_t)c.rves.size();
+        for (int lead = 1; lead >= 0; --lead) {
+            const size_t sm = lead ? mixed_lead_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit)
+                                   : mixed_fp32_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit);
+            const bool st = mixed_staged(lead, sm, c.part_max);
+            const size_t at = 2 * k + (lead ? 0 : 1);
+            if (smem) smem[at] = (int64_t)sm;
+            if (staged) staged[at] = st ? 1 : 0;
+            if (block) block[at] = mixed_block(0, lead != 0, st);
+        }
+    }
     return FE2_OK;
 }
 

@@ -1,0 +1,59 @@
+"""The mixed solver's launch plan, read back through the host-only
+fe2_batch_plan (no GPU needed)."""
+import numpy as np
+import pytest
+
+import rve_inputs as ri
+
+SMEM_OPTIN = 232448  # GB300 opt-in shared memory per block
+
+
+def test_benchmark_workload_runs_the_staged_kernels():
+    """64 RVEs of 5000 nodes: one class of 8-CTA clusters whose element
+    tables fit in shared memory for both kernels (the fast paths), 512
+    threads per CTA. A change that grows the per-node or per-element shared
+    memory past the budget would silently move this workload to the
+    re-reading fallback; this test catches it."""
+    import paper_2305_07030_gb300 as m
+    w = ri.equal_rves(64, 5000)
+    P = m.plan(w.nets, smem_optin=SMEM_OPTIN)
+    assert P["n_classes"] == 1 and list(P["parts"]) == [8] and list(P["rves"]) == [64]
+    assert P["staged"].tolist() == [[1, 1]]
+    assert P["block"].tolist() == [[512, 512]]
+    assert (P["smem"] <= SMEM_OPTIN - 16384).all()
+
+
+@pytest.mark.parametrize("target", [0, 256])
+def test_plan_is_consistent_with_the_layout(target):
+    import paper_2305_07030_gb300 as m
+    rng = np.random.default_rng(41)
+    nets = [ri.random_network(int(n), rng) for n in (37, 300, 777, 2100, 5000, 9000, 120)]
+    P = m.plan(nets, smem_optin=SMEM_OPTIN, nodes_per_cta=target)
+    L = m.layout(nets, smem_optin=SMEM_OPTIN, nodes_per_cta=target)
+    k = P["n_classes"]
+    assert sum(P["rves"]) == len(nets)
+    # one class per cluster size, and every RVE in the class of its size
+    assert len(set(P["parts"].tolist())) == k
+    for p in range(len(nets)):
+        assert P["parts"][P["rve_class"][p]] == L["parts"][p]
+    assert np.bincount(P["rve_class"], minlength=k).tolist() == P["rves"].tolist()
+    # every launch fits the shared-memory budget; the lead kernel without its
+    # table runs 256 threads per CTA, everything else 512
+    assert (P["smem"] <= SMEM_OPTIN - 16384).all()
+    for c in range(k):
+        lead_staged, fp32_staged = P["staged"][c]
+        assert P["block"][c, 0] == (512 if lead_staged else 256)
+        assert P["block"][c, 1] == 512
+
+
+def test_small_shared_memory_moves_classes_off_the_tables():
+    """With less shared memory the same RVEs need more parts or lose their
+    element tables; a plan never exceeds the budget."""
+    import paper_2305_07030_gb300 as m
+    rng = np.random.default_rng(42)
+    nets = [ri.random_network(int(n), rng) for n in (800, 1600)]
+    big = m.plan(nets, smem_optin=SMEM_OPTIN)
+    small_optin = 120 * 1000
+    small = m.plan(nets, smem_optin=small_optin)
+    assert (small["smem"] <= small_optin - 16384).all()
+    assert small["staged"].sum() <= big["staged"].sum()
