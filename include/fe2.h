@@ -63,12 +63,16 @@ typedef enum {
      * divide. The trajectory is bit for bit that of such an implementation;
      * only the residual and stress sums are reassociated. One CTA per RVE. */
     FE2_PREC_FP64 = 0,
-    /* All arithmetic on the FP32 pipes, one thread-block cluster per RVE: a
-     * double-float (FP32 pair) lead phase until the relative residual first
-     * drops below lead_tol (the transient in which the network picks its
-     * equilibrium), then FP32 increments of the element forces about a
-     * double-float reference state refreshed every rebase_every iterations.
-     * Residual test and stress sum are FP64. */
+    /* All iteration arithmetic on the FP32 pipes, one thread-block cluster
+     * of 1-16 CTAs per RVE: a double-float (FP32 pair) lead phase until the
+     * relative residual drops below lead_tol (the transient in which the
+     * network picks its equilibrium), then FP32 increments of the element
+     * forces about a double-float reference state refreshed every
+     * rebase_every iterations. The residual is totalled in double-float and
+     * compared with (tol f_ref)^2 formed in FP64; the stress sum is FP64.
+     * Each CTA holds its part's node state in shared memory, 120 bytes per
+     * node, which bounds an RVE to 16 parts of 1800 nodes (28,800 nodes) on
+     * a GB300; larger RVEs need FE2_PREC_FP64. */
     FE2_PREC_MIXED = 1
 } fe2_precision;
 

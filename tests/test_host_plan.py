@@ -57,3 +57,15 @@ def test_small_shared_memory_moves_classes_off_the_tables():
     small = m.plan(nets, smem_optin=small_optin)
     assert (small["smem"] <= small_optin - 16384).all()
     assert small["staged"].sum() <= big["staged"].sum()
+
+
+def test_mixed_path_size_limit():
+    """The mixed solver holds each part's node state in shared memory (120 B
+    per node), so on a GB300 an RVE fits in 16 parts of at most 1800 nodes:
+    28,800 nodes fit, 28,801 do not (the limit stated for FE2_PREC_MIXED)."""
+    import paper_2305_07030_gb300 as m
+    budget = SMEM_OPTIN - 16384
+    for n, fits in ((28_800, True), (28_801, False)):
+        P = m.plan([ri.random_network(n, np.random.default_rng(43))], smem_optin=SMEM_OPTIN)
+        assert list(P["parts"]) == [16]
+        assert bool((P["smem"] <= budget).all()) == fits, (n, P["smem"].tolist())
