@@ -393,7 +393,10 @@ def run_serving(args):
             "throughput_req_per_s": len(rve) / wall,
             "iters_first_step_mean": float(out["iters"][:n_pts].mean()),
             "iters_mean": float(out["iters"].mean()),
-            "status_ok": int((out["status"] == 0).sum())}
+            "status_ok": int((out["status"] == 0).sum()),
+            # [request, RVE, RVE nodes, status, iterations] of every request that did not converge
+            "not_ok": [[int(i), int(rve[i]), int(sizes[rve[i]]), int(out["status"][i]),
+                        int(out["iters"][i])] for i in np.nonzero(out["status"] != 0)[0]]}
 
 
 def main():
