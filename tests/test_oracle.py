@@ -209,6 +209,40 @@ def test_one_dof_chain_exact_trajectory():
     assert abs(net.X[1, 0] + r["u"][1, 0] - x_eq) <= 2e-6
 
 
+def test_kinetic_energy_exact_on_one_dof_chain():
+    """Algorithm 1's optional kinetic energy 1/2 sum m v^2 uses the full-step
+    velocity v_k = w + dt/2 a_k, a_k = (g(x_k) - c m w)/m, after the half-step
+    velocity w has moved the node to x_k. On the one-DOF chain this is exact
+    rational arithmetic; the oracle must match it."""
+    lam, EA1, EA2, c = Fraction(11, 10), Fraction(1), Fraction(2), Fraction(1, 8)
+    dt = Fraction(0.9)
+    L, x2 = Fraction(1, 2), lam
+    m = EA1 / (2 * L) + EA2 / (2 * L)
+
+    def g(x1):
+        return EA2 * ((x2 - x1) / L - 1) - EA1 * (x1 / L - 1)
+
+    x = lam * Fraction(1, 2)
+    w = dt / 2 * g(x) / m
+    kes = []
+    for _ in range(60):
+        x = x + dt * w
+        gx = g(x)
+        v_full = w + dt / 2 * (gx / m - c * w)
+        kes.append(m * v_full * v_full / 2)
+        w = (1 - c * dt) * w + dt * gx / m
+    X = [[0, 0, 0], [0.5, 0, 0], [1.0, 0, 0]]
+    net = _net(X, [[0, 1], [1, 2]], [1.0, 2.0], [1, 0, 1])
+    F = np.diag([1.1, 1.0, 1.0])
+    for k in (1, 2, 3, 10, 60):
+        r = oracle.solve(net, F, 0.125, init=1, max_iter=k, tol=1e-300, want_ke=True)
+        assert r["iters"] == k
+        assert math.isclose(r["ke"], float(kes[k - 1]), rel_tol=1e-12, abs_tol=1e-300), \
+            (k, r["ke"], float(kes[k - 1]))
+    # without the flag the energy is not tracked
+    assert oracle.solve(net, F, 0.125, init=1, max_iter=3, tol=1e-300)["ke"] == 0.0
+
+
 def test_status_maxiter_and_nan():
     rng = np.random.default_rng(5)
     net = ri.random_network(120, rng)
