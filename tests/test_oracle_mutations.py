@@ -25,6 +25,8 @@ MUTATIONS = {
                       "double V = V0;\n    for (int k = 0; k < 9; ++k) sigma[k] = s[k] / V;\n}\n\n/* The same"),
     "affine init ignored": ("if (fixed[i] || init == 1) u[3 * i + r] = uaff;",
                             "if (fixed[i]) u[3 * i + r] = uaff;"),
+    "kinetic energy without mass": ("ke += 0.5 * m[i] * (v[3 * i] * v[3 * i]",
+                                    "ke += 0.5 * (v[3 * i] * v[3 * i]"),
     "residual over all nodes": ("if (fixed[i]) continue;\n            for (int r = 0; r < 3; ++r) {\n                double fd",
                                 "for (int r = 0; r < 3; ++r) {\n                double fd"),
 }
