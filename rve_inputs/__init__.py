@@ -261,6 +261,21 @@ def uneven_rves(count: int, lo: int, hi: int, workload: int, first: int = 0,
                     np.array(cs), {"sizes": sizes, "lo": lo, "hi": hi})
 
 
+def uneven_subset(count: int, lo: int, hi: int, workload: int, idx) -> Workload:
+    """The RVEs ``idx`` of the uneven workload (same draws as uneven_rves)."""
+    sizes = log_uniform_sizes(np.random.Generator(np.random.PCG64(SEED_BASE + workload)),
+                              count, lo, hi)
+    nets, Fs, cs = [], [], []
+    for p in idx:
+        rng = _rve_rng(workload, int(p))
+        nets.append(random_network(int(sizes[p]), rng))
+        Fs.append(symmetric_perturbation(rng))
+        cs.append(default_damping(int(sizes[p])))
+    return Workload(f"uneven{lo}-{hi}x{count}[{len(nets)}]", nets,
+                    np.array(Fs).reshape(-1, 3, 3), np.array(cs),
+                    {"sizes": sizes, "lo": lo, "hi": hi, "idx": list(idx)})
+
+
 def uneven_sizes(count: int, lo: int, hi: int, workload: int) -> np.ndarray:
     return log_uniform_sizes(np.random.Generator(np.random.PCG64(SEED_BASE + workload)),
                              count, lo, hi)
