@@ -66,7 +66,7 @@ def _load():
             lib.oracle_stress_virial.argtypes = [I64, P, I64, P, P, P, P, D, P]
             lib.oracle_stress_boundary.argtypes = [I64, P, P, P, P, D, P]
             lib.oracle_dr_solve.argtypes = [I64, P, I64, P, P, P, P, D, D, I64, D, C.c_int, P, D,
-                                            C.c_int, P, P, P, P, P, P]
+                                            C.c_int, P, P, P, P, P, P, P, P]
             lib.oracle_dr_solve.restype = C.c_int
             lib.oracle_newton.argtypes = [I64, P, I64, P, P, P, P, C.c_int, D, P]
             lib.oracle_newton.restype = C.c_int
@@ -137,9 +137,11 @@ def stress_boundary(x, g, fixed, F, V0=1.0):
 
 
 def solve(net, F, c, tol=1e-8, max_iter=10_000_000, alpha=0.9, init=0, u_warm=None,
-          want_ke=False):
+          want_ke=False, want_energy=False):
     """Run Algorithm 1 on one network. Returns a dict with u (n,3), sigma (3,3),
-    iters, rel_res, f_ref, ke and status ("OK", "MAXITER", "NAN")."""
+    iters, rel_res, f_ref, ke, wint, wext and status ("OK", "MAXITER", "NAN").
+    want_energy also tracks the internal and external work of the energy
+    balance check (and the kinetic energy)."""
     X, el, EA, fx = _f64(net.X), _i32(net.elems), _f64(net.EA), _u8(net.fixed)
     F = _f64(F)
     n = X.shape[0]
@@ -148,18 +150,22 @@ def solve(net, F, c, tol=1e-8, max_iter=10_000_000, alpha=0.9, init=0, u_warm=No
     sig = np.zeros(9)
     iters = C.c_int64(0)
     rr, fr, ke = C.c_double(0), C.c_double(0), C.c_double(0)
+    wi, we = C.c_double(0), C.c_double(0)
+    mode = 2 if want_energy else int(bool(want_ke))
     st = _load().oracle_dr_solve(n, _p(X), el.shape[0], _p(el), _p(EA), _p(fx), _p(F), float(c),
                                  float(tol), int(max_iter), float(alpha), int(init), _p(uw),
-                                 float(net.V0), int(bool(want_ke)), _p(u), _p(sig),
-                                 C.byref(iters), C.byref(rr), C.byref(fr), C.byref(ke))
+                                 float(net.V0), mode, _p(u), _p(sig),
+                                 C.byref(iters), C.byref(rr), C.byref(fr), C.byref(ke),
+                                 C.byref(wi), C.byref(we))
     if st < 0:
         raise ValueError(f"oracle_dr_solve failed with {st}")
     return {"u": u, "sigma": sig.reshape(3, 3), "iters": iters.value, "rel_res": rr.value,
-            "f_ref": fr.value, "ke": ke.value, "status": STATUS[st]}
+            "f_ref": fr.value, "ke": ke.value, "wint": wi.value, "wext": we.value,
+            "status": STATUS[st]}
 
 
 def solve_batch(workload, tol=1e-8, max_iter=10_000_000, alpha=0.9, init=0, u_warm=None,
-                threads=None, want_ke=False):
+                threads=None, want_ke=False, want_energy=False):
     """Solve every RVE of a workload, one RVE per host thread (ctypes drops
     the GIL while the C solver runs)."""
     threads = threads or os.cpu_count() or 1
@@ -167,7 +173,7 @@ def solve_batch(workload, tol=1e-8, max_iter=10_000_000, alpha=0.9, init=0, u_wa
 
     def one(p):
         return solve(workload.nets[p], workload.F[p], workload.damping[p], tol, max_iter, alpha,
-                     init, uw[p], want_ke)
+                     init, uw[p], want_ke, want_energy)
 
     order = sorted(range(workload.n_rve), key=lambda p: -workload.nets[p].n_nodes)
     out = [None] * workload.n_rve

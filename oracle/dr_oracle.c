@@ -165,16 +165,29 @@ static double norm2(int64_t n, const double *g, const uint8_t *mask, int want) {
  * In : n, X (n*3), E, el (E*2, node ids), EA (E), fixed (n), F (9, row-major),
  *      c (damping), tol, max_iter (>= 1), alpha (time-step safety factor),
  *      init (0 reference, 1 affine, 2 warm), u_warm (n*3, used when init = 2),
- *      V0, want_ke (1: track kinetic energy).
+ *      V0, want_ke (1: track kinetic energy; 2: also the internal and
+ *      external work of the energy balance check).
  * Out: u (n*3, displacement at the last force evaluation), sigma (9),
- *      iters, rel_res (r / f_ref, 0 when f_ref = 0), f_ref, ke (last KE or 0).
+ *      iters, rel_res (r / f_ref, 0 when f_ref = 0), f_ref, ke (last KE or 0),
+ *      wint, wext (work since the start, 0 unless want_ke = 2; may be NULL).
+ *
+ * Energy balance (Algorithm 1, "optionally check energy balance": three
+ * reductions over the free DOFs per iteration). With du = dt v^(n-1/2) the
+ * step's displacement increment and f_d = -c m v^(n-1/2) the damping force:
+ *   kinetic   K    = 1/2 sum m |v^n|^2 (full-step velocity)
+ *   internal  Wint = Wint - 1/2 sum du . (g^(n-1) + g^n)   (energy stored;
+ *             g is the net internal force on a node, so -g resists)
+ *   external  Wext = Wext + 1/2 sum du . (f_d^(n-1) + f_d^n)  (work of the
+ *             damping forces; the prescribed nodes do not move while the
+ *             iteration runs, so their reactions do no work)
+ * trapezoidal in du, with g^0 the initial force and f_d^0 = 0.
  * Returns ORC_OK, ORC_MAXITER, ORC_NAN, or a negative error.
  */
 int oracle_dr_solve(int64_t n, const double *X, int64_t E, const int32_t *el, const double *EA,
                     const uint8_t *fixed, const double *F, double c, double tol, int64_t max_iter,
                     double alpha, int init, const double *u_warm, double V0, int want_ke,
                     double *u, double *sigma, int64_t *iters, double *rel_res, double *f_ref_out,
-                    double *ke_out) {
+                    double *ke_out, double *wint_out, double *wext_out) {
     if (n <= 0 || E < 0 || max_iter < 1) return ORC_EINVAL;
     double *L = malloc(sizeof(double) * (E ? E : 1));
     double *m = malloc(sizeof(double) * n);
@@ -183,8 +196,10 @@ int oracle_dr_solve(int64_t n, const double *X, int64_t E, const int32_t *el, co
     double *a = calloc(3 * n, sizeof(double));
     double *g = malloc(sizeof(double) * 3 * n);
     uint8_t *fx = malloc(n);
-    if (!L || !m || !x || !v || !a || !g || !fx) {
-        free(L); free(m); free(x); free(v); free(a); free(g); free(fx);
+    double *gp = want_ke == 2 ? calloc(3 * n, sizeof(double)) : NULL;   /* g^(n-1) */
+    double *fdp = want_ke == 2 ? calloc(3 * n, sizeof(double)) : NULL;  /* f_d^(n-1) */
+    if (!L || !m || !x || !v || !a || !g || !fx || (want_ke == 2 && (!gp || !fdp))) {
+        free(L); free(m); free(x); free(v); free(a); free(g); free(fx); free(gp); free(fdp);
         return ORC_ENOMEM;
     }
 
@@ -221,10 +236,12 @@ int oracle_dr_solve(int64_t n, const double *X, int64_t E, const int32_t *el, co
     for (int64_t i = 0; i < n; ++i)
         if (!fixed[i])
             for (int r = 0; r < 3; ++r) a[3 * i + r] = g[3 * i + r] / m[i];
+    if (want_ke == 2)
+        for (int64_t k = 0; k < 3 * n; ++k) gp[k] = g[k];
 
     int status = ORC_MAXITER;
     int64_t it = 0;
-    double r_norm = 0.0, ke = 0.0;
+    double r_norm = 0.0, ke = 0.0, wint = 0.0, wext = 0.0;
     for (;;) {
         /* compute next time step */
         double dt = oracle_time_step(E, EA, L, alpha);
@@ -241,17 +258,28 @@ int oracle_dr_solve(int64_t n, const double *X, int64_t E, const int32_t *el, co
         oracle_internal_forces(n, x, E, el, EA, L, g);
         /* damping force; force residual (free-DOF reduction); update
          * accelerations; partial velocity update */
-        double rs = 0.0;
+        double rs = 0.0, wi = 0.0, we = 0.0;
         for (int64_t i = 0; i < n; ++i) {
             if (fixed[i]) continue;
             for (int r = 0; r < 3; ++r) {
                 double fd = -c * m[i] * v[3 * i + r];
+                if (want_ke == 2) {
+                    /* energy check: this step's increment times the forces at
+                     * its two ends (v still holds v^(n-1/2) here) */
+                    double du = dt * v[3 * i + r];
+                    wi += du * (gp[3 * i + r] + g[3 * i + r]);
+                    we += du * (fdp[3 * i + r] + fd);
+                    gp[3 * i + r] = g[3 * i + r];
+                    fdp[3 * i + r] = fd;
+                }
                 rs += g[3 * i + r] * g[3 * i + r];
                 a[3 * i + r] = (g[3 * i + r] + fd) / m[i];
                 v[3 * i + r] += 0.5 * dt * a[3 * i + r];
             }
         }
         r_norm = sqrt(rs);
+        wint -= 0.5 * wi;
+        wext += 0.5 * we;
         /* optional energy check: kinetic part */
         if (want_ke) {
             ke = 0.0;
@@ -272,7 +300,9 @@ int oracle_dr_solve(int64_t n, const double *X, int64_t E, const int32_t *el, co
     *rel_res = f_ref > 0.0 ? r_norm / f_ref : (r_norm > 0.0 ? INFINITY : 0.0);
     *f_ref_out = f_ref;
     *ke_out = ke;
-    free(L); free(m); free(x); free(v); free(a); free(g); free(fx);
+    if (wint_out) *wint_out = wint;
+    if (wext_out) *wext_out = wext;
+    free(L); free(m); free(x); free(v); free(a); free(g); free(fx); free(gp); free(fdp);
     return status;
 }
 

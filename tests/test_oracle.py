@@ -243,6 +243,88 @@ def test_kinetic_energy_exact_on_one_dof_chain():
     assert oracle.solve(net, F, 0.125, init=1, max_iter=3, tol=1e-300)["ke"] == 0.0
 
 
+def _chain_energy_exact(k, lam, EA1, EA2, c, dt):
+    """Exact rational quantities of the one-DOF chain after k iterations: the
+    stored elastic energy change W(x_k) - W(x_0) (W = sum 1/2 EA L (l/L - 1)^2;
+    the bars stay on the x-axis, so W is quadratic in x and the trapezoid rule
+    of the oracle's work sum is exact for it), and the terms of the leapfrog's
+    discrete energy identity
+        1/2 m w_{k+1}^2 - 1/2 m w_1^2
+            = -Wint + Wext + 1/2 (g_k + f_k) du_{k+1} - 1/2 g_0 du_1,
+    with w_n the half-step velocity of step n, du_n = dt w_n, f_n = -c m w_n.
+    The identity follows from m (w_{n+1} - w_n) = dt (g_n + f_n) times
+    (w_{n+1} + w_n)/2, summed by parts; it fixes Wext given Wint."""
+    L = Fraction(1, 2)
+    x2 = lam
+    m = EA1 / (2 * L) + EA2 / (2 * L)
+
+    def g(x1):
+        return EA2 * ((x2 - x1) / L - 1) - EA1 * (x1 / L - 1)
+
+    def W(x1):
+        return EA1 * L * (x1 / L - 1) ** 2 / 2 + EA2 * L * ((x2 - x1) / L - 1) ** 2 / 2
+
+    x0 = lam * Fraction(1, 2)
+    g0 = g(x0)
+    w1 = dt / 2 * g0 / m
+    x, w = x0, w1
+    for _ in range(k):
+        x = x + dt * w
+        gx = g(x)
+        f = -c * m * w
+        w_next = w + dt * (gx + f) / m
+        w, g_last, f_last = w_next, gx, f
+    wint = W(x) - W(x0)
+    wext = m * w * w / 2 - m * w1 * w1 / 2 + wint - (g_last + f_last) * dt * w / 2 + g0 * dt * w1 / 2
+    return wint, wext
+
+
+def test_energy_balance_terms_exact_on_one_dof_chain():
+    """Algorithm 1's optional energy check, internal and external work: on the
+    one-DOF chain the internal work is the exact change of stored energy and
+    the damping work closes the leapfrog's discrete energy identity."""
+    lam, EA1, EA2, c = Fraction(11, 10), Fraction(1), Fraction(2), Fraction(1, 8)
+    dt = Fraction(0.9)
+    X = [[0, 0, 0], [0.5, 0, 0], [1.0, 0, 0]]
+    net = _net(X, [[0, 1], [1, 2]], [1.0, 2.0], [1, 0, 1])
+    F = np.diag([1.1, 1.0, 1.0])
+    for k in (1, 2, 3, 10, 60):
+        wint, wext = _chain_energy_exact(k, lam, EA1, EA2, c, dt)
+        r = oracle.solve(net, F, 0.125, init=1, max_iter=k, tol=1e-300, want_energy=True)
+        assert r["iters"] == k
+        assert math.isclose(r["wint"], float(wint), rel_tol=1e-11, abs_tol=1e-17), (k, r["wint"], wint)
+        assert math.isclose(r["wext"], float(wext), rel_tol=1e-9, abs_tol=1e-17), (k, r["wext"], wext)
+        assert r["wext"] < 0.0  # damping only removes energy
+    # the work sums are tracked only on request
+    r = oracle.solve(net, F, 0.125, init=1, max_iter=3, tol=1e-300, want_ke=True)
+    assert r["wint"] == 0.0 and r["wext"] == 0.0
+
+
+def test_energy_balance_terms_on_a_random_network():
+    """Without damping the external work is zero; the internal work follows
+    the stored energy sum(1/2 EA L (l/L - 1)^2) of the nonlinear network to
+    the trapezoid rule's accuracy at this time step."""
+    rng = np.random.default_rng(5)
+    net = ri.random_network(300, rng)
+    F = ri.symmetric_perturbation(rng)
+    a, b = net.elems[:, 0], net.elems[:, 1]
+    L = np.linalg.norm(net.X[b] - net.X[a], axis=1)
+
+    def W(x):
+        l = np.linalg.norm(x[b] - x[a], axis=1)
+        return float(np.sum(0.5 * net.EA * L * (l / L - 1.0) ** 2))
+
+    x0 = net.X @ F.T
+    for c, k in ((0.0, 400), (ri.default_damping(300), 3000)):
+        r = oracle.solve(net, F, c, init=1, max_iter=k, want_energy=True)
+        dW = W(net.X + r["u"]) - W(x0)
+        assert abs(r["wint"] - dW) <= 1e-2 * abs(dW), (c, r["wint"], dW)
+        if c == 0.0:
+            assert r["wext"] == 0.0
+        else:
+            assert r["wext"] < 0.0
+
+
 def test_status_maxiter_and_nan():
     rng = np.random.default_rng(5)
     net = ri.random_network(120, rng)
