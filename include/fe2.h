@@ -22,8 +22,14 @@
  *     reorderings never show in any input or output.
  *   - 3x3 tensors (F, sigma) are row-major, 9 doubles per RVE.
  *   - A batch owns all of its device memory until fe2_batch_destroy(). The
- *     library allocates only in create and destroy; solve allocates nothing.
+ *     library allocates only in create and destroy; solve allocates nothing
+ *     (the naive comparator, fe2_batch_solve_naive, allocates its scratch on
+ *     first use).
  *   - Calls on one batch must not run concurrently from several host threads.
+ *   - Serving submissions (fe2_batch_submit) and batched calls on the same
+ *     batch are ordered: a submission starts after the last batched solve,
+ *     a batched solve starts after every submission still in flight, and
+ *     the host readbacks wait for both.
  */
 #ifndef FE2_H
 #define FE2_H
@@ -53,7 +59,8 @@ typedef enum {
     FE2_RVE_OK = 0,      /* residual <= tol * f_ref */
     FE2_RVE_MAXITER = 1, /* max_iter iterations without converging */
     FE2_RVE_NAN = 2,     /* the residual became NaN or infinite */
-    FE2_RVE_PENDING = 3  /* not solved yet */
+    FE2_RVE_PENDING = 3  /* not solved yet (code 5 is internal: an RVE waiting
+                            for the double-float resume; never returned) */
 } fe2_rve_status;
 
 typedef enum {
@@ -70,9 +77,11 @@ typedef enum {
      * forces about a double-float reference state refreshed every
      * rebase_every iterations. The residual is totalled in double-float and
      * compared with (tol f_ref)^2 formed in FP64; the stress sum is FP64.
-     * Each CTA holds its part's node state in shared memory, 120 bytes per
-     * node, which bounds an RVE to 16 parts of 1800 nodes (28,800 nodes) on
-     * a GB300; larger RVEs need FE2_PREC_FP64. */
+     * Each CTA holds its part's node state in shared memory: 96 bytes per
+     * node for the FP32 kernel without its element table (velocity and
+     * acceleration then live in global memory), which bounds an RVE to 16
+     * parts of 2,186 nodes (34,976 nodes) on a GB300; a solve with a larger
+     * RVE returns FE2_EINVAL (use FE2_PREC_FP64). */
     FE2_PREC_MIXED = 1
 } fe2_precision;
 
@@ -98,13 +107,69 @@ typedef struct {
                              double-float iterations */
     int32_t rebase_every; /* MIXED: FP32 iterations between double-float
                              reference refreshes; <= 0 = default 512 */
-    int32_t reserved;
+    int32_t launch;       /* 0 = the batched solve replays a CUDA graph,
+                             captured by the first solve with this option
+                             set (default); 1 = plain stream launches */
     double lead_tol;      /* MIXED: relative residual that ends the lead
                              phase (default 1e-3) */
+    int64_t stall_window; /* MIXED: FP32 evaluations in which the squared
+                             residual must fall to a quarter of its reference
+                             value; when it does not (the FP32 increments have
+                             reached their rounding floor), the RVE is handed
+                             back to a double-float resume that runs to
+                             convergence. 0 = default 250,000; < 0 = never */
 } fe2_opts;
 
 /* Fill *opts with the defaults listed above. */
 void fe2_opts_default(fe2_opts *opts);
+
+/*
+ * Launch tuning of the mixed solver per RVE size bucket b, the RVEs with
+ * 2^b <= n_nodes < 2^(b+1): the cluster size (CTAs, i.e. spatial parts, per
+ * RVE; a power of two <= 16) and the CTA sizes of the FP32 and lead kernels
+ * (multiples of 32 in [64, 512]). Zero entries mean automatic: the smallest
+ * cluster whose parts hold at most 1024 nodes, doubled while the FP32
+ * kernel's element table does not fit in shared memory, and 512 threads.
+ * The paper found the best team size to depend on the sub-problem size
+ * (Section III); fe2_autotune measures it on this GPU.
+ *
+ * The setting is process-wide and applies to batches created, and plans
+ * computed, after the call. A configuration is a function of the RVE's size
+ * alone, so an RVE runs the same way in any batch; results change with it
+ * only by rounding (the partition and the grouping of partial sums).
+ */
+typedef struct {
+    int32_t parts[32];
+    int32_t block_fp32[32];
+    int32_t block_lead[32];
+} fe2_tuning;
+
+/* Set the process-wide tuning (NULL: every entry automatic). FE2_EINVAL for
+ * an entry out of range; nothing changes then. */
+fe2_status fe2_tuning_set(const fe2_tuning *t);
+/* Copy the current tuning into *t. */
+fe2_status fe2_tuning_get(fe2_tuning *t);
+/* Set the tuning from a JSON file written by fe2_autotune. FE2_EINVAL if the
+ * file cannot be read, is malformed, or was measured on another GPU model or
+ * SM count. */
+fe2_status fe2_tuning_load(const char *path);
+
+/*
+ * Autotuner of the mixed solver: for every size bucket present among the
+ * given sample RVEs, time bounded solves (trial_iters iterations, a quarter of
+ * them in the double-float lead) of the samples, replicated to fill the GPU,
+ * for each feasible cluster size and FP32-kernel CTA size in {256, 384, 512},
+ * and keep the pair with the most node-iterations per second per SM. The
+ * result is set as the process-wide tuning, returned in *out (may be NULL)
+ * and, if json_path is not NULL, written there as JSON keyed by GPU model,
+ * SM count, precision and bucket. Inputs as for fe2_batch_create, plus F
+ * (9*n_rve, row-major) for the trial solves. Synchronous; allocates and frees
+ * its trial batches.
+ */
+fe2_status fe2_autotune(int32_t n_rve, const int64_t *node_off, const double *X,
+                        const int64_t *elem_off, const int32_t *conn, const double *EA,
+                        const uint8_t *fixed, const double *damping, const double *F,
+                        int64_t trial_iters, const char *json_path, fe2_tuning *out);
 
 /*
  * Create a batch of n_rve networks (Algorithm 1: load mesh, compute edge and
@@ -317,6 +382,23 @@ fe2_status fe2_batch_kernel_times(fe2_batch *b, float *ms, int32_t cap, int32_t 
 fe2_status fe2_batch_solve_naive(fe2_batch *b, const double *F, const fe2_opts *opts,
                                  void *stream);
 
+/*
+ * Partition of a batch over n_ranks GPUs (Section I: every macroscale
+ * material point's microscale problem is independent, so the batch shards
+ * with no exchange during the iterations; only the 9-double stresses are
+ * gathered afterwards). Host only. Longest processing time first: RVEs in
+ * decreasing estimated cost, each to the least-loaded rank (ties: lower RVE
+ * id first, lower rank). Cost = n_nodes * iters[p] when iters is given and
+ * iters[p] > 0 (e.g. the previous solve's counts), else n_nodes^1.5 (the
+ * iteration count of these networks grows about like n^0.5).
+ * node_off  n_rve+1 prefix offsets (as in fe2_batch_create)
+ * iters     n_rve iteration counts, or NULL
+ * rank_of   out: n_rve rank of each RVE
+ * rank_cost out (may be NULL): n_ranks summed cost per rank
+ */
+fe2_status fe2_shard_plan(int32_t n_rve, const int64_t *node_off, const int64_t *iters,
+                          int32_t n_ranks, int32_t *rank_of, double *rank_cost);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *fe2_last_error(void);
 
@@ -330,7 +412,13 @@ const char *fe2_last_error(void);
  * 1.6 MB) that every GPU loading the library holds until the process exits.
  *
  * It runs the same per-RVE FP64 solver as fe2_batch_solve with
- * FE2_PREC_FP64, so results are bit-identical to that path, in one CTA.
+ * FE2_PREC_FP64, in one CTA. Every node's update is the same sequence of IEEE
+ * operations as on that path, but the free nodes are held in the caller's
+ * order rather than the batch's spatial order, so the residual sum is
+ * associated differently: rel_res agrees with the batched path to about
+ * 1e-12, and where the two iteration counts agree (they can differ by one
+ * when the residual lands within rounding of the threshold) the
+ * displacement is bit-identical and sigma agrees to about 1e-12.
  *
  * n_nodes    1 .. 4096 nodes;  n_elems  0 .. 16384 elements (else FE2_EINVAL)
  * X_dev      3*n_nodes reference coordinates, xyz interleaved

@@ -14,7 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Batch", "Opts", "last_error", "FE2Error", "LIB_PATH", "RVE_STATUS"]
+__all__ = ["Batch", "Opts", "Tuning", "last_error", "FE2Error", "LIB_PATH", "RVE_STATUS",
+           "tuning_get", "tuning_set", "tuning_load", "autotune", "shard_plan"]
 
 LIB_PATH = _build.LIB
 RVE_STATUS = {0: "OK", 1: "MAXITER", 2: "NAN", 3: "PENDING"}
@@ -28,17 +29,24 @@ class FE2Error(RuntimeError):
         self.code = code
 
 
+class Tuning(C.Structure):
+    """fe2_tuning: per size bucket b (2^b <= nodes < 2^(b+1)) the mixed
+    solver's cluster size and CTA sizes; zero = automatic."""
+    _fields_ = [("parts", C.c_int32 * 32), ("block_fp32", C.c_int32 * 32),
+                ("block_lead", C.c_int32 * 32)]
+
+
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("dt_safety", C.c_double),
                 ("precision", C.c_int32), ("init", C.c_int32), ("kinetic_energy", C.c_int32),
                 ("block_threads", C.c_int32), ("lead_iters", C.c_int64),
-                ("rebase_every", C.c_int32), ("reserved", C.c_int32), ("lead_tol", C.c_double)]
+                ("rebase_every", C.c_int32), ("launch", C.c_int32), ("lead_tol", C.c_double),
+                ("stall_window", C.c_int64)]
 
 
 def _load():
-    path = LIB_PATH
-    if not os.path.exists(path) or os.environ.get("FE2_REBUILD"):
-        path = _build.build()
+    # rebuilt when missing or older than any of its sources (a no-op otherwise)
+    path = _build.build(force=bool(os.environ.get("FE2_REBUILD")))
     lib = C.CDLL(path)
     P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     lib.fe2_opts_default.argtypes = [C.POINTER(Opts)]
@@ -63,6 +71,8 @@ def _load():
     lib.fe2_batch_plan.argtypes = [I32, P, P, P, P, P, P, I64, I32, I32, P, P, P, P, P, P, P]
     lib.fe2_probe_smem_bandwidth.argtypes = [P, P]
     lib.fe2_probe_smem_bandwidth.restype = C.c_int
+    lib.fe2_probe_fp64_rates.argtypes = [P, P, P]
+    lib.fe2_probe_fp64_rates.restype = C.c_int
     lib.fe2_rve_solve_noalloc.argtypes = [I32, I32, P, P, P, P, P, D, D, C.POINTER(Opts), P, P, P,
                                           P, P, P]
     lib.fe2_rve_solve_noalloc.restype = C.c_int
@@ -70,6 +80,11 @@ def _load():
     lib.fe2_noalloc_scratch_bytes.restype = C.c_size_t
     lib.fe2_noalloc_last_error.argtypes = []
     lib.fe2_noalloc_last_error.restype = C.c_char_p
+    lib.fe2_tuning_set.argtypes = [C.POINTER(Tuning)]
+    lib.fe2_tuning_get.argtypes = [C.POINTER(Tuning)]
+    lib.fe2_tuning_load.argtypes = [C.c_char_p]
+    lib.fe2_autotune.argtypes = [I32, P, P, P, P, P, P, P, P, I64, C.c_char_p, C.POINTER(Tuning)]
+    lib.fe2_shard_plan.argtypes = [I32, P, P, I32, P, P]
     lib.fe2_last_error.argtypes = []
     lib.fe2_last_error.restype = C.c_char_p
     for name in ("fe2_batch_create", "fe2_batch_solve", "fe2_batch_solve_dev",
@@ -77,7 +92,9 @@ def _load():
                  "fe2_batch_get_displacement", "fe2_batch_set_displacement",
                  "fe2_batch_destroy", "fe2_batch_info", "fe2_batch_kernel_times",
                  "fe2_batch_diagnostics", "fe2_batch_parts", "fe2_batch_submit",
-                 "fe2_batch_poll", "fe2_serve", "fe2_batch_layout", "fe2_batch_plan"):
+                 "fe2_batch_poll", "fe2_serve", "fe2_batch_layout", "fe2_batch_plan",
+                 "fe2_tuning_set", "fe2_tuning_get", "fe2_tuning_load", "fe2_autotune",
+                 "fe2_shard_plan"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -94,6 +111,16 @@ def probe_smem_bandwidth():
     return g.value, c.value
 
 
+def probe_fp64_rates():
+    """Measured aggregate FP64 throughput (operations/s) of fused multiply-add,
+    correctly rounded division and square root: (fma, div, sqrt)."""
+    f, d, q = C.c_double(), C.c_double(), C.c_double()
+    rc = _lib.fe2_probe_fp64_rates(C.byref(f), C.byref(d), C.byref(q))
+    if rc != 0:
+        raise FE2Error(3, f"fp64 probe failed ({rc})")
+    return f.value, d.value, q.value
+
+
 def rve_solve_noalloc(n_nodes, n_elems, X_dev, conn_dev, EA_dev, fixed_dev, F_dev, u_dev,
                       sigma_dev, iters_dev, rel_res_dev, status_dev, damping=-1.0, V0=1.0,
                       stream=None, **opts):
@@ -108,6 +135,59 @@ def rve_solve_noalloc(n_nodes, n_elems, X_dev, conn_dev, EA_dev, fixed_dev, F_de
                                     _stream_handle(stream))
     if rc != 0:
         raise FE2Error(rc, _lib.fe2_noalloc_last_error().decode())
+
+
+def tuning_get() -> dict:
+    """The process-wide launch tuning as {bucket: (parts, block_fp32, block_lead)}
+    for the buckets with a non-zero entry."""
+    t = Tuning()
+    _check(_lib.fe2_tuning_get(C.byref(t)))
+    return {b: (t.parts[b], t.block_fp32[b], t.block_lead[b]) for b in range(32)
+            if t.parts[b] or t.block_fp32[b] or t.block_lead[b]}
+
+
+def tuning_set(entries=None):
+    """Set the tuning from {bucket: (parts, block_fp32[, block_lead])};
+    None resets every entry to automatic."""
+    if entries is None:
+        _check(_lib.fe2_tuning_set(None))
+        return
+    t = Tuning()
+    for b, v in entries.items():
+        t.parts[b] = int(v[0])
+        t.block_fp32[b] = int(v[1]) if len(v) > 1 else 0
+        t.block_lead[b] = int(v[2]) if len(v) > 2 else 0
+    _check(_lib.fe2_tuning_set(C.byref(t)))
+
+
+def tuning_load(path):
+    _check(_lib.fe2_tuning_load(os.fsencode(path)))
+
+
+def autotune(nets, F, damping=None, trial_iters=2000, json_path=None):
+    """Run fe2_autotune on sample RVEs; returns the chosen tuning (also set
+    process-wide and, with json_path, written as JSON)."""
+    node_off, X, elem_off, conn, EA, fixed = _pack_inputs(nets)
+    Fh = np.ascontiguousarray(F, np.float64).reshape(len(nets), 9)
+    damp = None if damping is None else np.ascontiguousarray(damping, np.float64)
+    t = Tuning()
+    _check(_lib.fe2_autotune(len(nets), _ptr(node_off), _ptr(X), _ptr(elem_off), _ptr(conn),
+                             _ptr(EA), _ptr(fixed), _ptr(damp), _ptr(Fh), int(trial_iters),
+                             None if json_path is None else os.fsencode(json_path), C.byref(t)))
+    return tuning_get()
+
+
+def shard_plan(node_counts, n_ranks, iters=None):
+    """fe2_shard_plan: the rank of every RVE (LPT by estimated cost) and the
+    summed cost per rank."""
+    counts = np.asarray(node_counts, np.int64)
+    node_off = np.ascontiguousarray(np.concatenate([[0], np.cumsum(counts)]), np.int64)
+    it = None if iters is None else np.ascontiguousarray(iters, np.int64)
+    rank_of = np.zeros(len(counts), np.int32)
+    cost = np.zeros(int(n_ranks))
+    _check(_lib.fe2_shard_plan(len(counts), _ptr(node_off), _ptr(it), int(n_ranks), _ptr(rank_of),
+                               _ptr(cost)))
+    return rank_of, cost
 
 
 def last_error() -> str:
@@ -129,7 +209,7 @@ _INIT = {"reference": 0, "affine": 1, "warm": 2}
 
 def make_opts(tol=1e-8, max_iter=10_000_000, dt_safety=0.9, precision="mixed", init="affine",
               kinetic_energy=False, block_threads=0, lead_iters=-1, rebase_every=0,
-              lead_tol=1e-3) -> Opts:
+              lead_tol=1e-3, launch="graph", stall_window=0) -> Opts:
     o = Opts()
     _lib.fe2_opts_default(C.byref(o))
     o.tol = float(tol)
@@ -142,6 +222,8 @@ def make_opts(tol=1e-8, max_iter=10_000_000, dt_safety=0.9, precision="mixed", i
     o.lead_iters = int(lead_iters)
     o.rebase_every = int(rebase_every)
     o.lead_tol = float(lead_tol)
+    o.launch = {"graph": 0, "stream": 1}[launch] if isinstance(launch, str) else int(launch)
+    o.stall_window = int(stall_window)
     return o
 
 
@@ -360,10 +442,10 @@ class Batch:
 
     def kernel_times_ms(self):
         """Event-timed duration of each persistent launch of the last solve."""
-        buf = np.zeros(16, np.float32)
+        buf = np.zeros(512, np.float32)
         n = C.c_int32()
-        _check(_lib.fe2_batch_kernel_times(self._h, _ptr(buf), 16, C.byref(n)))
-        return [float(x) for x in buf[:min(n.value, 16)]]
+        _check(_lib.fe2_batch_kernel_times(self._h, _ptr(buf), 512, C.byref(n)))
+        return [float(x) for x in buf[:min(n.value, 512)]]
 
     def close(self):
         if getattr(self, "_h", None):

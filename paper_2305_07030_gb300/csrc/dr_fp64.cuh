@@ -5,7 +5,50 @@
 
 namespace fe2 {
 
-template <bool SM>
+// Force of every element with a free end on its first node (caller
+// orientation a -> b): t_e = (N/l) d, d = x_b - x_a, in the operations of
+// gather_force_fp64. Node b's gather would compute d' = -d exactly, the same
+// l, N and q, and q d' = -t_e exactly, so summing +-t_e in a node's row order
+// reproduces its gather bit for bit with half the square roots and divisions.
+__device__ __forceinline__ void element_forces_fp64(const DevMesh &M, const RveDesc &R, int nf,
+                                                    const double *x0, const double *x1,
+                                                    const double *x2, double *tf) {
+    for (int e = threadIdx.x; e < R.n_elems; e += blockDim.x) {
+        const int64_t ee = R.elem0 + e;
+        const int a = M.el_a[ee], b = M.el_b[ee];
+        if (a >= nf && b >= nf) continue;  // both ends fixed: no free node needs it
+        const double d0 = dsub(x0[b], x0[a]), d1 = dsub(x1[b], x1[a]), d2 = dsub(x2[b], x2[a]);
+        const double l = dsqrt(dadd(dadd(dmul(d0, d0), dmul(d1, d1)), dmul(d2, d2)));
+        const double N = dmul(M.el_EA[ee], dsub(ddiv(l, M.el_L[ee]), 1.0));
+        const double q = ddiv(N, l);
+        double *t = tf + 3 * ee;
+        t[0] = dmul(q, d0);
+        t[1] = dmul(q, d1);
+        t[2] = dmul(q, d2);
+    }
+}
+
+// Node i's internal force from the element forces, in its CSR row order.
+__device__ __forceinline__ void gather_table_fp64(const DevMesh &M, const RveDesc &R,
+                                                  const int32_t *rowptr, int i, const double *tf,
+                                                  double &g0, double &g1, double &g2) {
+    const int beg = rowptr[i], end = rowptr[i + 1];
+    const double *tr = tf + 3 * R.elem0;
+    g0 = 0.0; g1 = 0.0; g2 = 0.0;
+    for (int k = beg; k < end; ++k) {
+        const int w = M.csr_el[R.csr0 + k];
+        const double *t = tr + 3 * (w >> 1);
+        if (w & 1) {
+            g0 = dsub(g0, t[0]); g1 = dsub(g1, t[1]); g2 = dsub(g2, t[2]);
+        } else {
+            g0 = dadd(g0, t[0]); g1 = dadd(g1, t[1]); g2 = dadd(g2, t[2]);
+        }
+    }
+}
+
+// ET: element forces through the per-element table S.tf (batched path);
+// otherwise every directed edge is evaluated by gather_force_fp64.
+template <bool SM, bool ET>
 __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevResults &O,
                                const SolveParams &P, int p, double *smem, double *red) {
     const RveDesc R = M.rve[p];
@@ -104,11 +147,16 @@ __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevRes
             x2[i] = dadd(X2[i], uu2);
         }
         __syncthreads();
+        if (ET) {
+            element_forces_fp64(M, R, nf, x0, x1, x2, S.tf);
+            __syncthreads();
+        }
         // getInternalForces; damping force; residual; accelerations; velocity
         double rs = 0.0, kes = 0.0;
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
             double g0, g1, g2;
-            gather_force_fp64(M, rowptr, R.csr0, i, x0, x1, x2, g0, g1, g2);
+            if (ET) gather_table_fp64(M, R, rowptr, i, S.tf, g0, g1, g2);
+            else gather_force_fp64(M, rowptr, R.csr0, i, x0, x1, x2, g0, g1, g2);
             const double m = mass[i];
             const double cm = dmul(mc, m);
             double vv0 = v0[i], vv1 = v1[i], vv2 = v2[i];

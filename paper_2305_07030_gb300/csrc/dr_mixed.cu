@@ -48,6 +48,11 @@
 // exactly opposite values, so this equals the per-direction evaluation.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "df64.cuh"
 #include "dr_device.cuh"
 
@@ -60,9 +65,12 @@ namespace {
 constexpr int kMaxWarps = 16;  // blocks of at most 512 threads
 constexpr int kLeadBufs = 3;   // lead kernel: rotating partial buffers
 constexpr int kBufs = 5;       // FP32 kernel: rotating increment / partial buffers
-// FP32 kernel shared memory per staged node: reference position, five
-// increment buffers (float4 each), velocity + a.x (float4), a.yz (float2).
+// FP32 kernel shared memory per node with the element table: reference
+// position, five increment buffers (float4 each), velocity + a.x (float4),
+// a.yz (float2). Without the table, velocity and acceleration live in global
+// memory and a node takes the first six float4 only.
 constexpr size_t kFp32NodeBytes = (1 + kBufs + 1) * sizeof(float4) + sizeof(float2);
+constexpr size_t kFp32PlainNodeBytes = (1 + kBufs) * sizeof(float4);
 // Lead kernel shared memory per node without the element table: one
 // double-float displacement (hi, lo float4); with the table, two of them.
 constexpr size_t kLeadPlainNodeBytes = 2 * sizeof(float4);
@@ -92,6 +100,10 @@ struct MixedShared {
     float *kredp[kMaxParts];                  // every CTA's kred
     double *sigp;                             // rank 0's sig
     int item;
+    // FP32 kernel stall tracker (testing warp): the squared residual that the
+    // next ones must reach a quarter of, and the evaluation that set it
+    float st_h, st_l;
+    long long st_e;
     int elems;                                // FP32 kernel: elements of this CTA's part
     int slots;                                // FP32 kernel: row slots of this CTA's part
 };
@@ -557,6 +569,7 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
                                  int elem_cap, int slot_cap, const df &lead2, const df &thresh2,
                                  const df &dt, const df &hdt, const df &cdf, int64_t &it,
                                  int &status, df &r2, df &k2) {
+    const int64_t it0 = it;  // evaluations before this call (resume: > 0)
     const int n = R.n_nodes, m = pt.m();
     const int64_t n0 = R.node0, b3 = 3 * n0;
     const int32_t *rowptr = M.rowptr + R.rp0;
@@ -621,7 +634,7 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
                 Lc[k] = make_float4(u[0].lo, u[1].lo, u[2].lo, 0.f);
             }
         }
-        const bool test_now = nidx >= 3;
+        const bool test_now = nidx >= it0 + 3;  // two evaluations of this call published
         cluster_arrive();
         if (test_now && test_warp) {
             const Verdict v = residual_verdict(sh, pt, (int)((nidx - 2) & 3), 0, lead2, want_k, INT64_MAX);
@@ -707,6 +720,85 @@ __device__ void lead_loop_staged(cg::cluster_group &cl, MixedShared &sh, const D
     }
 }
 
+// End of a mixed solve of RVE p: the final displacement (FP64 output; the
+// double-float displacement plus the FP32 increment Qfin when given), the
+// FP64 stress sum split across the cluster, and the per-RVE outputs.
+__device__ void mixed_finish(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
+                             const DevResults &O, const SolveParams &P, int p, const RveDesc &R,
+                             const Part &pt, const double *F, const float4 *Qfin, int status, int64_t it,
+                             df r2, df k2, double f_ref) {
+    const int n = R.n_nodes, m = pt.m();
+    const int64_t n0 = R.node0, b3 = 3 * n0;
+    const float *uh = S.uh + b3, *ul = S.ul + b3;
+    double *xg = S.xg + b3;
+    const bool want_k = P.want_ke != 0;
+    const int fin = Qfin ? 0 : -1;
+    // ---- final displacement (FP64 output) and positions for the stress ----
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int i = pt.gidx(k);
+        float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (fin >= 0 && k < pt.nfr) d = Qfin[k];
+        const float dd[3] = {d.x, d.y, d.z};
+        double *uo[3] = {S.u0 + n0, S.u1 + n0, S.u2 + n0};
+        const double *Xd[3] = {M.X0 + n0, M.X1 + n0, M.X2 + n0};
+        for (int c = 0; c < 3; ++c) {
+            df u = {uh[c * n + i], ul[c * n + i]};
+            if (fin >= 0 && k < pt.nfr) u = df_add_f(u, dd[c]);
+            const double ud = df_to_double(u);
+            uo[c][i] = ud;
+            xg[c * n + i] = dadd(Xd[c][i], ud);
+        }
+    }
+    cl.sync();
+    // stress: elements split across the cluster, partials reduced on rank 0
+    double s[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s[k] = 0.0;
+    {
+        const double *x0 = xg, *x1 = xg + n, *x2 = xg + 2 * n;
+        for (int e = pt.me * blockDim.x + threadIdx.x; e < R.n_elems; e += pt.C * blockDim.x) {
+            const int64_t ee = R.elem0 + e;
+            const int a = M.el_a[ee], bb = M.el_b[ee];
+            double d[3] = {dsub(x0[bb], x0[a]), dsub(x1[bb], x1[a]), dsub(x2[bb], x2[a])};
+            const double l = dsqrt(dadd(dadd(dmul(d[0], d[0]), dmul(d[1], d[1])), dmul(d[2], d[2])));
+            const double q = ddiv(dmul(M.el_EA[ee], dsub(ddiv(l, M.el_L[ee]), 1.0)), l);
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) s[3 * rr + c] = dadd(s[3 * rr + c], dmul(dmul(q, d[rr]), d[c]));
+        }
+    }
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double v = s[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sh.wsum[warp][k] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double t = 0.0;
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += sh.wsum[w][threadIdx.x];
+        sh.sigp[pt.me * 9 + threadIdx.x] = t;
+    }
+    cl.sync();
+    if (pt.me == 0 && threadIdx.x < 9) {
+        double t = 0.0;
+        for (int q = 0; q < pt.C; ++q) t += sh.sig[q][threadIdx.x];
+        O.sigma[9 * (int64_t)p + threadIdx.x] = ddiv(t, dmul(det3(F), R.V0));
+    }
+    if (pt.me == 0 && threadIdx.x == 0) {
+        const double r = sqrt(df_to_double(r2));
+        O.iters[p] = it;
+        O.rel_res[p] = f_ref > 0.0 ? r / f_ref : (r > 0.0 ? INFINITY : 0.0);
+        O.status[p] = status;
+        O.ke[p] = want_k ? df_to_double(k2) : 0.0;
+    }
+    cl.sync();
+}
+
 // ---------------------------------------------------------------------------
 // lead kernel: setup (Algorithm 1 lines up to the loop) and the double-float
 // iterations
@@ -727,7 +819,23 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
     float *ah = S.ah + b3, *al = S.al + b3, *fg = S.fg + b3;
     const float *imh = M.imh + n0, *iml = M.iml + n0;
     const bool want_k = P.want_ke != 0;
-
+    double f_ref = 0.0;
+    int64_t it = 0;
+    if (P.resume) {
+        // resume launch: only RVEs the FP32 phase handed back, from the state
+        // it left (double-float displacement, velocity, acceleration)
+        const int st0 = O.status[p];
+        f_ref = O.f_ref[p];
+        it = O.iters[p];
+        cl.sync();  // every CTA has read the status before rank 0 rewrites it
+        if (st0 != RVE_STALLED) return;
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const int i = pt.gidx(k);
+            Pl[k] = make_float4(uh[i], uh[n + i], uh[2 * n + i], 0.f);
+            Q0[k] = make_float4(ul[i], ul[n + i], ul[2 * n + i], 0.f);
+        }
+        cl.sync();
+    } else {
     // affine displacement (F - I) X for f_ref, and the initial displacement
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int i = pt.gidx(k);
@@ -787,19 +895,36 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
     cl.sync();
     const double f0 = sqrt(df_to_double(cluster_total(sh.red, rb, pt.C)));
     rb = (rb + 1) % kLeadBufs;
-    const double f_ref = f_aff > f0 ? f_aff : f0;
+    f_ref = f_aff > f0 ? f_aff : f0;
+    }
     const df thresh2 = df_from_double(dmul(dmul(P.tol, f_ref), dmul(P.tol, f_ref)));
-    const df lead2 = df_from_double(dmul(dmul(P.lead_tol, f_ref), dmul(P.lead_tol, f_ref)));
+    // a resumed RVE runs in double-float until it converges
+    const df lead2 = P.resume ? thresh2 : df_from_double(dmul(dmul(P.lead_tol, f_ref), dmul(P.lead_tol, f_ref)));
+    const int64_t lead_iters = P.resume ? -1 : P.lead_iters;
     const double dt64 = dmul(P.alpha, R.dtc);
     const df dt = df_from_double(dt64), hdt = df_from_double(dmul(0.5, dt64));
     const df cdf = df_from_double(R.c);
 
-    int64_t it = 0;
+    const int64_t it0 = it;
     int status = RVE_PENDING;
     df r2 = df_from(0.f), k2 = df_from(0.f);
     if (STAGE) {
-        lead_loop_staged(cl, sh, M, S, R, pt, P, Pl, st, part_cap, elem_cap, slot_cap, lead2, thresh2,
-                         dt, hdt, cdf, it, status, r2, k2);
+        SolveParams Q = P;
+        Q.lead_iters = lead_iters;
+        for (;;) {
+            lead_loop_staged(cl, sh, M, S, R, pt, Q, Pl, st, part_cap, elem_cap, slot_cap, lead2, thresh2,
+                             dt, hdt, cdf, it, status, r2, k2);
+            // The loop stops two evaluations after the tested one; when
+            // resuming, the state it stops at must itself be converged, else
+            // the iteration goes on from that state.
+            if (!P.resume || status != RVE_PENDING) break;
+            for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                const int i = pt.gidx(k);
+                Pl[k] = make_float4(uh[i], uh[n + i], uh[2 * n + i], 0.f);
+                Q0[k] = make_float4(ul[i], ul[n + i], ul[2 * n + i], 0.f);
+            }
+            cl.sync();
+        }
     } else {
     // L lanes share a node's edges; lane 0 of group k owns node k's state in
     // every phase, so consecutive phases need no barrier between them.
@@ -855,8 +980,13 @@ __device__ void lead_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         if (!isfinite(r2.hi)) { status = RVE_NAN; break; }
         if (df_le(r2, thresh2)) { status = RVE_OK; break; }
         if (it >= P.max_iter) { status = RVE_MAXITER; break; }
-        if (P.lead_iters >= 0 ? it >= P.lead_iters : df_le(r2, lead2)) break;
+        if (lead_iters >= 0 ? it >= lead_iters : df_le(r2, lead2)) break;
     }
+    }
+    if (P.resume) {
+        if (pt.me == 0 && threadIdx.x == 0) O.lead[p] += it - it0;
+        mixed_finish(cl, sh, M, S, O, P, p, R, pt, F, nullptr, status, it, r2, k2, f_ref);
+        return;
     }
     if (pt.me == 0 && threadIdx.x == 0) {
         O.iters[p] = it;
@@ -887,17 +1017,21 @@ __device__ __forceinline__ void next_increment(float w0, float w1, float w2, flo
 template <bool STAGE>
 __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &M, const DevState &S,
                          const DevResults &O, const SolveParams &P, int p, float4 *Pl,
-                         float4 *const *Qb, float4 *SV, float2 *SA, const Staged &st, int elem_cap,
+                         float4 *const *Qb, float4 *SVs, float2 *SAs, const Staged &st, int elem_cap,
                          int slot_cap, uint32_t bstride) {
     const RveDesc R = M.rve[p];
     const Part pt = make_part(M, R, p, (int)cl.block_rank(), (int)cl.num_blocks());
     const int n = R.n_nodes, m = pt.m();
     const int64_t n0 = R.node0, b3 = 3 * n0;
     const int32_t *rowptr = M.rowptr + R.rp0;
+    // velocity (+ a.x) and a.yz of the own free nodes: shared memory with the
+    // element table; otherwise global (L2-resident) arrays, which keeps the
+    // unstaged kernel's shared memory at 96 bytes per node
+    float4 *SV = STAGE ? SVs : S.sv + n0 + pt.f0;
+    float2 *SA = STAGE ? SAs : S.sa + n0 + pt.f0;
     const float *Xh = M.Xh + b3, *Xl = M.Xl + b3;
     float *uh = S.uh + b3, *ul = S.ul + b3, *vh = S.vh + b3, *ah = S.ah + b3, *fg = S.fg + b3;
     const float *imh = M.imh + n0;
-    double *xg = S.xg + b3;
     const bool want_k = P.want_ke != 0;
     double F[9];
 #pragma unroll
@@ -948,6 +1082,11 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             element_counts(M, R, pt, rowptr, st);
             __syncthreads();
             if (threadIdx.x == 0) element_offsets(sh, pt, st);
+        }
+        if (threadIdx.x == 0) {
+            sh.st_h = INFINITY;
+            sh.st_l = 0.f;
+            sh.st_e = it;
         }
         cl.sync();
         int n_el = 0;
@@ -1014,7 +1153,24 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
             Verdict mine = {-1, 0.f, 0.f, 0.f, 0.f};
             if (chk <= nidx - 3) {
                 if (rebase || test_warp) mine = residual_verdict(sh, pt, chkb, chk + 1, thresh2, want_k, P.max_iter);
-                if (!rebase && test_warp && lane == 0) sh.vd[b] = mine;
+                if (!rebase && test_warp && lane == 0) {
+                    // Stall check: the squared residual must reach a quarter of
+                    // its reference value within stall_window evaluations,
+                    // else the RVE goes back to the double-float kernel (the
+                    // FP32 increments have hit their rounding floor). Every
+                    // CTA's testing warp sees the same verdicts, so all agree.
+                    if (mine.code < 0 && P.stall_window > 0) {
+                        const df r2c = {mine.r2h, mine.r2l};
+                        if (df_le(r2c, {0.25f * sh.st_h, 0.25f * sh.st_l})) {
+                            sh.st_h = r2c.hi;
+                            sh.st_l = r2c.lo;
+                            sh.st_e = chk;
+                        } else if (chk - sh.st_e >= P.stall_window) {
+                            mine.code = RVE_STALLED;
+                        }
+                    }
+                    sh.vd[b] = mine;
+                }
                 tnow = true; teval = chk; tbuf = chkb;
                 ++chk;
                 chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
@@ -1044,6 +1200,31 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
                     ++chk;
                     chkb = chkb + 1 == kBufs ? 0 : chkb + 1;
                 }
+            }
+            if (stopv.code == RVE_STALLED) {
+                // Hand back at the end of evaluation nidx-1, whose state is
+                // complete: displacement = double-float base + its increment
+                // (buffer bp), acceleration a, full-step velocity = SV - dt/2 a.
+                const float4 *inc = Qb[bp];
+                for (int k = grp; k < pt.nfr; k += ngrp) {
+                    if (sub != 0) continue;
+                    const int i = pt.f0 + k;
+                    const float4 d = inc[k], va = SV[k];
+                    const float2 ay = SA[k];
+                    const float dd[3] = {d.x, d.y, d.z}, vv[3] = {va.x, va.y, va.z}, aa[3] = {va.w, ay.x, ay.y};
+                    for (int c = 0; c < 3; ++c) {
+                        const df u = df_add_f({uh[c * n + i], ul[c * n + i]}, dd[c]);
+                        uh[c * n + i] = u.hi;
+                        ul[c * n + i] = u.lo;
+                        S.vh[b3 + c * n + i] = vv[c] - hdtf * aa[c];
+                        S.vl[b3 + c * n + i] = 0.f;
+                        S.ah[b3 + c * n + i] = aa[c];
+                        S.al[b3 + c * n + i] = 0.f;
+                    }
+                }
+                status = RVE_STALLED;
+                it = nidx - 1;
+                break;
             }
             if (stopv.code >= 0) {
                 status = stopv.code;
@@ -1211,70 +1392,17 @@ __device__ void fp32_rve(cg::cluster_group &cl, MixedShared &sh, const DevMesh &
         }
     }
 
-    // ---- final displacement (FP64 output) and positions for the stress ----
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        const int i = pt.gidx(k);
-        float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (fin >= 0 && k < pt.nfr) d = Qb[fin][k];
-        const float dd[3] = {d.x, d.y, d.z};
-        double *uo[3] = {S.u0 + n0, S.u1 + n0, S.u2 + n0};
-        const double *Xd[3] = {M.X0 + n0, M.X1 + n0, M.X2 + n0};
-        for (int c = 0; c < 3; ++c) {
-            df u = {uh[c * n + i], ul[c * n + i]};
-            if (fin >= 0 && k < pt.nfr) u = df_add_f(u, dd[c]);
-            const double ud = df_to_double(u);
-            uo[c][i] = ud;
-            xg[c * n + i] = dadd(Xd[c][i], ud);
+    if (status == RVE_STALLED) {
+        // handed back to the double-float kernel (resume launch), which
+        // finishes the solve and writes every output
+        if (pt.me == 0 && threadIdx.x == 0) {
+            O.iters[p] = it;
+            O.status[p] = RVE_STALLED;
         }
+        cl.sync();
+        return;
     }
-    cl.sync();
-    // stress: elements split across the cluster, partials reduced on rank 0
-    double s[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s[k] = 0.0;
-    {
-        const double *x0 = xg, *x1 = xg + n, *x2 = xg + 2 * n;
-        for (int e = pt.me * blockDim.x + threadIdx.x; e < R.n_elems; e += pt.C * blockDim.x) {
-            const int64_t ee = R.elem0 + e;
-            const int a = M.el_a[ee], bb = M.el_b[ee];
-            double d[3] = {dsub(x0[bb], x0[a]), dsub(x1[bb], x1[a]), dsub(x2[bb], x2[a])};
-            const double l = dsqrt(dadd(dadd(dmul(d[0], d[0]), dmul(d[1], d[1])), dmul(d[2], d[2])));
-            const double q = ddiv(dmul(M.el_EA[ee], dsub(ddiv(l, M.el_L[ee]), 1.0)), l);
-#pragma unroll
-            for (int rr = 0; rr < 3; ++rr)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) s[3 * rr + c] = dadd(s[3 * rr + c], dmul(dmul(q, d[rr]), d[c]));
-        }
-    }
-    {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            double v = s[k];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) sh.wsum[warp][k] = v;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 9) {
-        double t = 0.0;
-        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) t += sh.wsum[w][threadIdx.x];
-        sh.sigp[pt.me * 9 + threadIdx.x] = t;
-    }
-    cl.sync();
-    if (pt.me == 0 && threadIdx.x < 9) {
-        double t = 0.0;
-        for (int q = 0; q < pt.C; ++q) t += sh.sig[q][threadIdx.x];
-        O.sigma[9 * (int64_t)p + threadIdx.x] = ddiv(t, dmul(det3(F), R.V0));
-    }
-    if (pt.me == 0 && threadIdx.x == 0) {
-        const double r = sqrt(df_to_double(r2));
-        O.iters[p] = it;
-        O.rel_res[p] = f_ref > 0.0 ? r / f_ref : (r > 0.0 ? INFINITY : 0.0);
-        O.status[p] = status;
-        O.ke[p] = want_k ? df_to_double(k2) : 0.0;
-    }
-    cl.sync();
+    mixed_finish(cl, sh, M, S, O, P, p, R, pt, F, fin >= 0 ? Qb[fin] : nullptr, status, it, r2, k2, f_ref);
 }
 
 }  // namespace
@@ -1318,7 +1446,7 @@ __global__ void __launch_bounds__(512, 1) dr_mixed_lead_kernel(DevMesh M, DevSta
     map_remote(cl, sh, Pl, Qb, (int)cl.num_blocks());
     int rb = 0;
     for (;;) {
-        const int item = next_item(cl, sh, P.counter);
+        const int item = next_item(cl, sh, P.counter + (P.resume ? 2 : 0));
         if (item >= P.queue_len) return;
         lead_rve<STAGE>(cl, sh, M, S, O, P, P.queue[item], Pl, Q0, st, part_cap, elem_cap, slot_cap, rb);
     }
@@ -1386,18 +1514,31 @@ cudaLaunchConfig_t mixed_config(int clusters, int parts, int block, size_t smem,
     return cfg;
 }
 
+// Raise a kernel's dynamic shared-memory limit (and allow 16-CTA clusters)
+// once per device and size, so that launches recorded into a CUDA graph make
+// no attribute calls of their own.
+std::mutex g_prep_mutex;
+std::map<std::pair<const void *, int>, int> g_prep_bytes;  // (kernel, device) -> limit set
+
 template <class K>
 void prepare(K kernel, size_t smem) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_prep_mutex);
+    int &have = g_prep_bytes[{reinterpret_cast<const void *>(kernel), dev}];
+    if (have < (int)smem || have == 0) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        have = std::max(have, (int)smem);
+    }
 }
 }  // namespace
 
 size_t mixed_fp32_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, size_t limit) {
-    const size_t plain = kFp32NodeBytes * (size_t)part_cap;
+    const size_t plain = kFp32PlainNodeBytes * (size_t)part_cap;
     const size_t F = (size_t)free_cap, U = (size_t)elem_cap, S = (size_t)slot_cap;
-    const size_t staged =
-        align16(align16(plain) + 16 * F + 3 * 16 * U + 4 * U + 4 * S + 2 * 4 * F + 4 * (F / 32 + 2));
+    const size_t staged = align16(align16(kFp32NodeBytes * (size_t)part_cap) + 16 * F + 3 * 16 * U +
+                                  4 * U + 4 * S + 2 * 4 * F + 4 * (F / 32 + 2));
     return staged <= limit ? staged : plain;
 }
 
@@ -1410,8 +1551,10 @@ size_t mixed_lead_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, s
 }
 
 bool mixed_staged(int lead, size_t smem, int part_cap) {
-    return smem > (lead ? kLeadPlainNodeBytes : kFp32NodeBytes) * (size_t)part_cap;
+    return smem > (lead ? kLeadPlainNodeBytes : kFp32PlainNodeBytes) * (size_t)part_cap;
 }
+
+size_t mixed_plain_node_bytes(int lead) { return lead ? kLeadPlainNodeBytes : kFp32PlainNodeBytes; }
 
 int launch_dr_mixed(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
                     int lead, int clusters, int parts, int block, size_t smem, int part_cap,

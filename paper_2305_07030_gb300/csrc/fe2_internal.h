@@ -61,6 +61,9 @@ struct DevMesh {
     const float4 *dh, *dl;        // per CSR entry: (X_j - X_i, L) as double-float hi / lo
     const int32_t *el_a, *el_b;   // stress elements (RVE-local permuted ids)
     const double *el_EA, *el_L;
+    const int32_t *csr_el;        // per CSR entry: RVE-local element << 1, | 1 when
+                                  // the row's node is the element's second node
+                                  // (caller orientation)
 };
 
 // Mutable solver state (device).
@@ -73,6 +76,9 @@ struct DevState {
     float *ah, *al;               // MIXED: acceleration (same convention)
     float *fg;                    // MIXED: reference force g_ref, FP32 [3][N]
     double *xg;                   // [3][N] FP64 positions scratch
+    double *tf;                   // FP64: per element, its force on the first node (3)
+    float4 *sv;                   // MIXED FP32 kernel without element table: per node
+    float2 *sa;                   //   (v, a.x) and (a.y, a.z)
 };
 
 struct DevResults {
@@ -97,11 +103,19 @@ struct SolveParams {
     int rebase_every;
     const int32_t *queue; // RVE ids in scheduling order
     int32_t queue_len;
-    int32_t *counter;     // work-queue heads (zeroed before the launch; mixed uses two)
+    int32_t *counter;     // work-queue heads (zeroed before the launch; mixed uses three)
     int smem_positions;   // FP64 kernel: 1 = positions staged in shared memory
+    int64_t stall_window; // MIXED: FP32 evaluations without the squared residual
+                          // falling to a quarter before the RVE is handed back
+                          // to double-float; 0 = never
+    int resume;           // MIXED lead kernel: 1 = resume launch (stalled RVEs only)
 };
 
-enum { RVE_OK = 0, RVE_MAXITER = 1, RVE_NAN = 2, RVE_PENDING = 3 };
+// RVE_STALLED (internal): the FP32 phase stopped making progress and the RVE
+// waits for the double-float resume launch, which replaces the status.
+enum { RVE_OK = 0, RVE_MAXITER = 1, RVE_NAN = 2, RVE_PENDING = 3, RVE_STALLED = 5 };
+// Work-queue heads per launch class: lead, FP32 phase, double-float resume.
+constexpr int kCountersPerClass = 3;
 
 // Kernel launchers (defined in the .cu files).
 int launch_setup(int32_t n_rve, int64_t n_el, int64_t n_csr, RveDesc *rve,
@@ -128,6 +142,8 @@ size_t mixed_fp32_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, s
 size_t mixed_lead_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, size_t limit);
 // Whether a launch with `smem` bytes uses the shared-memory element table.
 bool mixed_staged(int lead, size_t smem, int part_cap);
+// Shared memory per node of a kernel without its element table.
+size_t mixed_plain_node_bytes(int lead);
 // Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.
 int occupancy_dr_fp64(int smem_positions, int block, size_t smem);
 int occupancy_dr_mixed(int lead, int parts, int block, size_t smem, int part_cap);

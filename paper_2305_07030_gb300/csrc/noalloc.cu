@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kNaThreads) k_noalloc_solve(NaArgs A, SolvePar
 
     // ---- checks of the device-side inputs; degrees ----
     if (threadIdx.x == 0) err = 0;
+    __syncthreads();  // the flag is clear before any thread may set it
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         deg[i] = 0;
         const double *x = A.X + 3 * i;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kNaThreads) k_noalloc_solve(NaArgs A, SolvePar
     DevResults O = {};
     O.sigma = A.sigma; O.iters = A.iters; O.rel_res = A.rel_res; O.status = A.status;
     O.f_ref = misc; O.ke = misc + 1;
-    solve_rve_fp64<true>(M, S, O, P, 0, reinterpret_cast<double *>(smem_raw), red);
+    solve_rve_fp64<true, false>(M, S, O, P, 0, reinterpret_cast<double *>(smem_raw), red);
 
     // ---- displacement back in the caller's order ----
     for (int pi = threadIdx.x; pi < n; pi += blockDim.x) {

@@ -14,7 +14,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <numeric>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <vector>
@@ -60,6 +62,10 @@ struct DevBuf {
 // One size class: RVEs solved by one persistent launch.
 struct SizeClass {
     int parts = 1;              // mixed: cluster size
+    bool lead_staged = false;   // mixed: lead kernel with its element table
+    bool fp32_staged = false;   // mixed: FP32 kernel with its element table
+    int block_lead = 0;         // mixed: tuned CTA sizes (0 = default)
+    int block_fp32 = 0;
     int smem_positions = 1;     // FP64: positions in shared memory
     size_t smem_bytes = 0;      // dynamic shared memory per CTA
     int part_max = 0;           // mixed: largest part (nodes)
@@ -114,10 +120,11 @@ struct fe2_batch {
     DevBuf<RveDesc> d_rve;
     DevBuf<double> d_X, d_mass, d_EA_csr, d_L_csr, d_el_EA, d_el_L;
     DevBuf<float> d_Xh, d_Xl, d_imh, d_iml;
-    DevBuf<int32_t> d_rowptr, d_col, d_col_part, d_part_off, d_el_a, d_el_b;
-    DevBuf<float2> d_eaf, d_eaf_lo;
+    DevBuf<int32_t> d_rowptr, d_col, d_col_part, d_part_off, d_el_a, d_el_b, d_csr_el;
+    DevBuf<float2> d_eaf, d_eaf_lo, d_sa;
+    DevBuf<float4> d_sv;
     DevBuf<float4> d_dh, d_dl;
-    DevBuf<double> d_u, d_v, d_a, d_xg;
+    DevBuf<double> d_u, d_v, d_a, d_xg, d_tf;
     DevBuf<float> d_uh, d_ul, d_vh, d_vl, d_ah, d_al, d_fg;
     DevBuf<double> d_F, d_sigma, d_rel, d_fref, d_ke;
     DevBuf<int64_t> d_iters, d_lead;
@@ -144,6 +151,15 @@ struct fe2_batch {
     std::vector<ServeSlot> slots;
     std::vector<uint8_t> in_flight;
     std::vector<int32_t> class_of_fp64, class_of_mixed;  // RVE -> class index
+    // resident CTAs (FP64) or clusters (mixed) per launch shape, queried once
+    // so that nothing but launches happens while a solve is captured
+    std::map<std::tuple<int, int, int, size_t, int>, int> occ;
+    // the batched solve as a CUDA graph, valid for the options it was
+    // captured with (the kernels read F, queues and state from device memory)
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t cap = nullptr;           // private capture stream
+    fe2_opts graph_opts = {};
+    int graph_launches = 0, graph_timed = 0;
 
     DevMesh mesh() const {
         DevMesh m;
@@ -170,6 +186,7 @@ struct fe2_batch {
         m.el_b = d_el_b.p;
         m.el_EA = d_el_EA.p;
         m.el_L = d_el_L.p;
+        m.csr_el = d_csr_el.p;
         return m;
     }
     DevState state() const {
@@ -180,6 +197,9 @@ struct fe2_batch {
         s.uh = d_uh.p; s.ul = d_ul.p; s.vh = d_vh.p; s.vl = d_vl.p;
         s.ah = d_ah.p; s.al = d_al.p; s.fg = d_fg.p;
         s.xg = d_xg.p;
+        s.tf = d_tf.p;
+        s.sv = d_sv.p;
+        s.sa = d_sa.p;
         return s;
     }
     DevResults results() const {
@@ -192,7 +212,7 @@ struct fe2_batch {
         d_rve.release(); d_X.release(); d_mass.release(); d_EA_csr.release(); d_L_csr.release();
         d_el_EA.release(); d_el_L.release(); d_Xh.release(); d_Xl.release(); d_imh.release();
         d_iml.release(); d_rowptr.release(); d_col.release(); d_col_part.release();
-        d_part_off.release(); d_el_a.release(); d_el_b.release(); d_eaf.release();
+        d_part_off.release(); d_el_a.release(); d_el_b.release(); d_csr_el.release(); d_tf.release(); d_sv.release(); d_sa.release(); d_eaf.release();
         d_eaf_lo.release(); d_dh.release(); d_dl.release(); d_u.release(); d_v.release(); d_a.release(); d_xg.release();
         d_uh.release(); d_ul.release(); d_vh.release(); d_vl.release(); d_ah.release();
         d_al.release(); d_fg.release(); d_F.release(); d_sigma.release(); d_rel.release();
@@ -206,6 +226,10 @@ struct fe2_batch {
         aux = nullptr;
         if (ev_done) cudaEventDestroy(ev_done);
         ev_done = nullptr;
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+        if (cap) cudaStreamDestroy(cap);
+        cap = nullptr;
         if (h_iters) cudaFreeHost(h_iters);
         h_iters = nullptr;
         if (h_queue) cudaFreeHost(h_queue);
@@ -250,6 +274,7 @@ void fe2_opts_default(fe2_opts *o) {
     o->lead_iters = -1;
     o->rebase_every = 0;
     o->lead_tol = 1e-3;
+    o->stall_window = 0;
 }
 
 const char *fe2_last_error(void) { return g_err.c_str(); }
@@ -260,20 +285,27 @@ namespace {
 
 bool finite3(const double *p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
-// Shared-memory bytes per staged node of the mixed solver's FP32 kernel
-// (reference position and five rotating increment buffers, float4 each;
-// velocity and acceleration, float4 + float2); it bounds the part size.
-constexpr size_t kMixedNodeBytes = 120;
-
-// Number of cluster CTAs for an RVE of n nodes in the mixed solver: a power
-// of two with about `target` nodes per CTA, enough parts for the staged state
-// to fit in shared memory, at most 16.
-int choose_parts(int n, int target, size_t smem_cap) {
+// Smallest cluster size (CTAs) for an RVE of n nodes in the mixed solver: a
+// power of two with at most `target` nodes per CTA and room for the node
+// state of the FP32 kernel without its element table (the larger of the two
+// kernels' plain footprints, with slack for an uneven bisection), at most 16.
+int min_parts(int n, int target, size_t smem_cap) {
+    const size_t per_node = std::max(mixed_plain_node_bytes(0), mixed_plain_node_bytes(1));
     int C = 1;
-    while (C < kMaxParts &&
-           ((n + C - 1) / C > target || kMixedNodeBytes * ((n + C - 1) / C + 64) > smem_cap))
+    while (C < kMaxParts && ((n + C - 1) / C > target || per_node * ((n + C - 1) / C + 64) > smem_cap))
         C *= 2;
     return C;
+}
+
+// Process-wide launch tuning of the mixed solver per node-count bucket (log2
+// of the node count), set by fe2_tuning_set, fe2_tuning_load or fe2_autotune;
+// zero entries are automatic. Read when a batch is created.
+fe2_tuning g_tuning = {};
+
+int node_bucket(int n) {
+    int b = 0;
+    while (b < 31 && ((int64_t)2 << b) <= n) ++b;
+    return b;  // 2^b <= n < 2^(b+1)
 }
 
 // Recursive coordinate bisection of `ids` into `parts` (a power of two) sets.
@@ -330,21 +362,61 @@ void build_classes(const std::vector<RveDesc> &rve, const std::vector<int32_t> &
         for (auto &c : cls)
             if (!c.rves.empty()) out.push_back(c);
     } else {
-        std::vector<SizeClass> cls(5);  // parts 1, 2, 4, 8, 16
-        for (int k = 0; k < 5; ++k) cls[k].parts = 1 << k;
+        // A class is keyed by the cluster size and by whether each kernel keeps
+        // its element table in shared memory, both decided by the RVE alone
+        // (its own parts and table sizes), so an RVE runs the same code path,
+        // with the same CTA size, whatever batch it is in. RVEs of one key are
+        // packed first-fit into classes whose combined tables still fit.
+        const size_t limit = cap;
+        auto fits = [&](const SizeClass &c) {
+            const bool l = !c.lead_staged || mixed_staged(1, mixed_lead_smem(c.part_max, c.free_max, c.elem_max,
+                                                                             c.slot_max, limit), c.part_max);
+            const bool f = !c.fp32_staged || mixed_staged(0, mixed_fp32_smem(c.part_max, c.free_max, c.elem_max,
+                                                                             c.slot_max, limit), c.part_max);
+            return l && f;
+        };
         for (int32_t p : order) {
-            int k = 0;
-            while ((1 << k) < rve[p].n_parts) ++k;
-            SizeClass &c = cls[k];
-            c.rves.push_back(p);
-            c.part_max = std::max(c.part_max, rve[p].part_max);
-            c.free_max = std::max(c.free_max, part_free_max[p]);
-            c.elem_max = std::max(c.elem_max, rve[p].part_elem_max);
-            c.slot_max = std::max(c.slot_max, rve[p].part_slot_max);
-            c.smem_bytes = kMixedNodeBytes * c.part_max;
+            const RveDesc &R = rve[p];
+            SizeClass one;
+            one.parts = R.n_parts;
+            one.part_max = R.part_max;
+            one.free_max = part_free_max[p];
+            one.elem_max = R.part_elem_max;
+            one.slot_max = R.part_slot_max;
+            one.lead_staged = mixed_staged(1, mixed_lead_smem(one.part_max, one.free_max, one.elem_max,
+                                                              one.slot_max, limit), one.part_max);
+            one.fp32_staged = mixed_staged(0, mixed_fp32_smem(one.part_max, one.free_max, one.elem_max,
+                                                              one.slot_max, limit), one.part_max);
+            const int bk = node_bucket(R.n_nodes);
+            one.block_lead = g_tuning.block_lead[bk];
+            one.block_fp32 = g_tuning.block_fp32[bk];
+            bool placed = false;
+            for (auto &c : out) {
+                if (c.parts != one.parts || c.lead_staged != one.lead_staged || c.fp32_staged != one.fp32_staged ||
+                    c.block_lead != one.block_lead || c.block_fp32 != one.block_fp32)
+                    continue;
+                SizeClass t = c;
+                t.part_max = std::max(t.part_max, one.part_max);
+                t.free_max = std::max(t.free_max, one.free_max);
+                t.elem_max = std::max(t.elem_max, one.elem_max);
+                t.slot_max = std::max(t.slot_max, one.slot_max);
+                if (!fits(t)) continue;
+                t.rves.push_back(p);
+                c = std::move(t);
+                placed = true;
+                break;
+            }
+            if (!placed) {
+                one.rves.push_back(p);
+                out.push_back(std::move(one));
+            }
         }
-        for (auto &c : cls)
-            if (!c.rves.empty()) out.push_back(c);
+        // the class holding the largest RVEs (longest critical path) first
+        std::stable_sort(out.begin(), out.end(), [](const SizeClass &a, const SizeClass &b) {
+            return a.parts > b.parts;
+        });
+        for (auto &c : out)
+            c.smem_bytes = mixed_plain_node_bytes(0) * c.part_max;
     }
     int32_t off = 0;
     for (auto &c : out) {
@@ -354,6 +426,23 @@ void build_classes(const std::vector<RveDesc> &rve, const std::vector<int32_t> &
 }
 
 int mixed_block(int requested, bool lead, bool staged);
+
+// Dynamic shared memory of a mixed class's lead (lead = 1) or FP32 kernel:
+// with the element table when the class is staged for that kernel.
+size_t class_smem(const SizeClass &c, int lead, size_t limit) {
+    const bool st = lead ? c.lead_staged : c.fp32_staged;
+    if (!st) return mixed_plain_node_bytes(lead) * (size_t)c.part_max;
+    return lead ? mixed_lead_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit)
+                : mixed_fp32_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit);
+}
+
+// CTA size of a mixed class's kernel: the caller's request, else the tuned
+// size of its RVEs' size bucket, else the default.
+int class_block(const SizeClass &c, int lead, int requested) {
+    const bool st = lead ? c.lead_staged : c.fp32_staged;
+    const int tuned = lead ? c.block_lead : c.block_fp32;
+    return mixed_block(requested ? requested : tuned, lead != 0, st);
+}
 
 // Input validation of fe2_batch_create and the inspection calls (host only).
 fe2_status validate_batch(int32_t n_rve, const int64_t *node_off, const double *X,
@@ -410,7 +499,7 @@ struct HostLayout {
     std::vector<int64_t> perm_to_orig;   // permuted global -> caller global node
     std::vector<int32_t> part_free_max;  // per RVE, most free nodes in one part
     std::vector<double> X, EAcsr, ElEA;  // X as SoA [3][N]
-    std::vector<int32_t> col, colp, Ela, Elb, row, part;
+    std::vector<int32_t> col, colp, Ela, Elb, row, part, csrEl;
     std::vector<int64_t> ElemOf, Ga, Gb;
 };
 
@@ -426,6 +515,7 @@ void build_layout(int32_t n_rve, const int64_t *node_off, const double *X, const
     L.ElEA.assign(E, 0.0);
     L.col.assign(2 * E, 0);
     L.colp.assign(2 * E, 0);
+    L.csrEl.assign(2 * E, 0);
     L.Ela.assign(E, 0);
     L.Elb.assign(E, 0);
     L.ElemOf.assign(2 * E, 0);
@@ -446,58 +536,93 @@ void build_layout(int32_t n_rve, const int64_t *node_off, const double *X, const
         for (int64_t e = e0; e < e0 + ne; ++e) { deg[conn[2 * e]]++; deg[conn[2 * e + 1]]++; }
         std::vector<uint8_t> fx(n);
         for (int i = 0; i < n; ++i) fx[i] = (fixed[base + i] != 0) || deg[i] == 0;
-        const int C = choose_parts(n, target, smem_cap);
-        std::vector<int> all(n);
-        std::iota(all.begin(), all.end(), 0);
-        std::vector<std::vector<int>> parts;
-        rcb(all, C, X, base, parts);
-        // order: free nodes part by part (degree-sorted), then fixed part by part
-        std::vector<int> order;
-        order.reserve(n);
-        std::vector<int> owner(n), local(n);
-        int32_t *pf = hpart.data() + (size_t)p * 2 * (kMaxParts + 1);
-        int32_t *pg = pf + (kMaxParts + 1);
-        std::vector<std::vector<int>> fr(C), fxd(C);
-        for (int r = 0; r < C; ++r) {
-            for (int i : parts[r]) (fx[i] ? fxd[r] : fr[r]).push_back(i);
-            std::stable_sort(fr[r].begin(), fr[r].end(), [&](int x, int y) {
-                return deg[x] > deg[y] || (deg[x] == deg[y] && x < y);
-            });
-            std::sort(fxd[r].begin(), fxd[r].end());
-        }
-        int nfree = 0, part_max = 0, free_max = 0;
-        for (int r = 0; r < C; ++r) {
-            pf[r] = nfree;
-            for (size_t k = 0; k < fr[r].size(); ++k) {
-                owner[fr[r][k]] = r;
-                local[fr[r][k]] = (int)k;
-                order.push_back(fr[r][k]);
-            }
-            nfree += (int)fr[r].size();
-            part_max = std::max(part_max, (int)(fr[r].size() + fxd[r].size()));
-            free_max = std::max(free_max, (int)fr[r].size());
-        }
-        for (int r = C; r <= kMaxParts; ++r) pf[r] = nfree;
-        int nfixed = 0;
-        for (int r = 0; r < C; ++r) {
-            pg[r] = nfixed;
-            for (size_t k = 0; k < fxd[r].size(); ++k) {
-                owner[fxd[r][k]] = r;
-                local[fxd[r][k]] = (int)(fr[r].size() + k);
-                order.push_back(fxd[r][k]);
-            }
-            nfixed += (int)fxd[r].size();
-        }
-        for (int r = C; r <= kMaxParts; ++r) pg[r] = nfixed;
-        std::vector<int> newid(n);
-        for (int k = 0; k < n; ++k) newid[order[k]] = k;
-        // CSR rows in permuted order, entries sorted by ORIGINAL neighbour id
+        // CSR rows (caller ids), independent of the partition
         std::vector<std::vector<std::pair<int, int64_t>>> rows(n);
         for (int64_t e = e0; e < e0 + ne; ++e) {
             const int a = conn[2 * e], c = conn[2 * e + 1];
             rows[a].push_back({c, e});
             rows[c].push_back({a, e});
         }
+        for (auto &row : rows) std::sort(row.begin(), row.end());
+        // Parts: the smallest cluster that holds the plain state, doubled
+        // (up to 16) while the FP32 kernel's element table does not fit in
+        // shared memory; the autotuner may fix the count per size bucket.
+        int C = min_parts(n, target, smem_cap);
+        const int want = g_tuning.parts[node_bucket(n)];
+        const bool forced = want >= C && want <= kMaxParts && (want & (want - 1)) == 0;
+        if (forced) C = want;
+        std::vector<std::vector<int>> fr, fxd;
+        std::vector<int> owner(n), local(n);
+        int part_max = 0, free_max = 0, elem_max = 0, slot_max = 0;
+        for (;;) {
+            std::vector<int> all(n);
+            std::iota(all.begin(), all.end(), 0);
+            std::vector<std::vector<int>> parts;
+            rcb(all, C, X, base, parts);
+            fr.assign(C, {});
+            fxd.assign(C, {});
+            for (int r = 0; r < C; ++r) {
+                for (int i : parts[r]) (fx[i] ? fxd[r] : fr[r]).push_back(i);
+                std::stable_sort(fr[r].begin(), fr[r].end(), [&](int x, int y) {
+                    return deg[x] > deg[y] || (deg[x] == deg[y] && x < y);
+                });
+                std::sort(fxd[r].begin(), fxd[r].end());
+                for (size_t k = 0; k < fr[r].size(); ++k) { owner[fr[r][k]] = r; local[fr[r][k]] = (int)k; }
+                for (size_t k = 0; k < fxd[r].size(); ++k) {
+                    owner[fxd[r][k]] = r;
+                    local[fxd[r][k]] = (int)(fr[r].size() + k);
+                }
+            }
+            // FP32 kernel tables per part: elements with an end among the part's
+            // free nodes, once each (an element between two of them counted at
+            // its lower local index), and row slots in slabs of 32 free nodes,
+            // each 32 slots wide per entry of its longest row
+            part_max = free_max = elem_max = slot_max = 0;
+            for (int r = 0; r < C; ++r) {
+                part_max = std::max(part_max, (int)(fr[r].size() + fxd[r].size()));
+                free_max = std::max(free_max, (int)fr[r].size());
+                int elems = 0, slots = 0;
+                for (size_t k = 0; k < fr[r].size(); ++k) {
+                    const int i = fr[r][k];
+                    for (const auto &pr : rows[i]) {
+                        const int j = pr.first;
+                        elems += !(owner[j] == r && !fx[j] && local[j] < (int)k);
+                    }
+                }
+                for (size_t k0 = 0; k0 < fr[r].size(); k0 += 32) {
+                    int w = 0;
+                    for (size_t k = k0; k < k0 + 32 && k < fr[r].size(); ++k) w = std::max(w, deg[fr[r][k]]);
+                    slots += 32 * w;
+                }
+                elem_max = std::max(elem_max, elems);
+                slot_max = std::max(slot_max, slots);
+            }
+            const bool staged = mixed_staged(0, mixed_fp32_smem(part_max, free_max, elem_max, slot_max, smem_cap),
+                                             part_max);
+            if (staged || C >= kMaxParts || forced) break;
+            C *= 2;
+        }
+        // order: free nodes part by part (degree-sorted), then fixed part by part
+        std::vector<int> order;
+        order.reserve(n);
+        int32_t *pf = hpart.data() + (size_t)p * 2 * (kMaxParts + 1);
+        int32_t *pg = pf + (kMaxParts + 1);
+        int nfree = 0;
+        for (int r = 0; r < C; ++r) {
+            pf[r] = nfree;
+            for (int i : fr[r]) order.push_back(i);
+            nfree += (int)fr[r].size();
+        }
+        for (int r = C; r <= kMaxParts; ++r) pf[r] = nfree;
+        int nfixed = 0;
+        for (int r = 0; r < C; ++r) {
+            pg[r] = nfixed;
+            for (int i : fxd[r]) order.push_back(i);
+            nfixed += (int)fxd[r].size();
+        }
+        for (int r = C; r <= kMaxParts; ++r) pg[r] = nfixed;
+        std::vector<int> newid(n);
+        for (int k = 0; k < n; ++k) newid[order[k]] = k;
         RveDesc &R = L.rve[p];
         R.node0 = base;
         R.rp0 = base + p;
@@ -512,28 +637,6 @@ void build_layout(int32_t n_rve, const int64_t *node_off, const double *X, const
         R.V0 = V0 ? V0[p] : 1.0;
         R.part_max = part_max;
         R.part_free_max = free_max;
-        // FP32 kernel tables per part: elements with an end among the part's
-        // free nodes, once each (an element between two of them counted at its
-        // lower local index), and row slots in slabs of 32 free nodes, each 32
-        // slots wide per entry of its longest row
-        int elem_max = 0, slot_max = 0;
-        for (int r = 0; r < C; ++r) {
-            int elems = 0, slots = 0;
-            for (size_t k = 0; k < fr[r].size(); ++k) {
-                const int i = fr[r][k];
-                for (const auto &pr : rows[i]) {
-                    const int j = pr.first;
-                    elems += !(owner[j] == r && !fx[j] && local[j] < (int)k);
-                }
-            }
-            for (size_t k0 = 0; k0 < fr[r].size(); k0 += 32) {
-                int w = 0;
-                for (size_t k = k0; k < k0 + 32 && k < fr[r].size(); ++k) w = std::max(w, deg[fr[r][k]]);
-                slots += 32 * w;
-            }
-            elem_max = std::max(elem_max, elems);
-            slot_max = std::max(slot_max, slots);
-        }
         R.part_elem_max = elem_max;
         R.part_slot_max = slot_max;
         L.part_free_max[p] = free_max;
@@ -549,6 +652,7 @@ void build_layout(int32_t n_rve, const int64_t *node_off, const double *X, const
                 hcol[csr_pos + pos] = newid[pr.first];
                 hcolp[csr_pos + pos] = (owner[pr.first] << 16) | local[pr.first];
                 hElemOf[csr_pos + pos] = pr.second;
+                L.csrEl[csr_pos + pos] = (int32_t)(((pr.second - e0) << 1) | (conn[2 * pr.second + 1] == orig ? 1 : 0));
                 hEAcsr[csr_pos + pos] = EA[pr.second];
                 ++pos;
             }
@@ -638,6 +742,10 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     A(b->d_dl.alloc(2 * E), "dl");
     A(b->d_col.alloc(2 * E), "col");
     A(b->d_col_part.alloc(2 * E), "col_part");
+    A(b->d_csr_el.alloc(2 * E), "csr_el");
+    A(b->d_tf.alloc(3 * E), "tf");
+    A(b->d_sv.alloc(N), "sv");
+    A(b->d_sa.alloc(N), "sa");
     A(b->d_rowptr.alloc(N + n_rve), "rowptr");
     A(b->d_part_off.alloc(hpart.size()), "part_off");
     A(b->d_el_a.alloc(E), "el_a");
@@ -664,7 +772,7 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     A(b->d_lead.alloc(n_rve), "lead");
     A(b->d_status.alloc(n_rve), "status");
     A(b->d_queue.alloc(2 * (size_t)n_rve), "queue");
-    A(b->d_counters.alloc(32), "counters");
+    A(b->d_counters.alloc(kCountersPerClass * (size_t)n_rve + 16), "counters");
     A(d_elemof.alloc(2 * E), "elemof");
     A(d_ga.alloc(E), "ga");
     A(d_gb.alloc(E), "gb");
@@ -676,6 +784,7 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     H2D(b->d_EA_csr.p, hEAcsr.data(), sizeof(double) * 2 * E, "EA_csr");
     H2D(b->d_col.p, hcol.data(), sizeof(int32_t) * 2 * E, "col");
     H2D(b->d_col_part.p, hcolp.data(), sizeof(int32_t) * 2 * E, "col_part");
+    H2D(b->d_csr_el.p, L.csrEl.data(), sizeof(int32_t) * 2 * E, "csr_el");
     H2D(b->d_rowptr.p, hrow.data(), sizeof(int32_t) * (N + n_rve), "rowptr");
     H2D(b->d_part_off.p, hpart.data(), sizeof(int32_t) * hpart.size(), "part_off");
     H2D(b->d_el_a.p, hEla.data(), sizeof(int32_t) * E, "el_a");
@@ -714,8 +823,9 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         A(cudaMallocHost(&b->h_queue, sizeof(int32_t) * 2 * n_rve), "pinned queue");
         A(cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking), "aux stream");
         A(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming), "done event");
+        A(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
     }
-    for (int k = 0; k < 6 && rc == FE2_OK; ++k) {
+    for (int k = 0; k < 8 && rc == FE2_OK; ++k) {
         cudaStream_t s;
         A(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
         if (rc == FE2_OK) b->side.push_back(s);
@@ -733,7 +843,7 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
             A(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking), "slot stream");
             A(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "slot event");
             A(cudaMalloc(&sl.d_ids, sizeof(int32_t) * 2 * n_rve), "slot ids");
-            A(cudaMalloc(&sl.d_cnt, sizeof(int32_t) * 32), "slot counters");
+            A(cudaMalloc(&sl.d_cnt, sizeof(int32_t) * (kCountersPerClass * (size_t)n_rve + 16)), "slot counters");
             A(cudaMalloc(&sl.d_F, sizeof(double) * 9 * n_rve), "slot F");
             A(cudaMalloc(&sl.d_out, sizeof(double) * 10 * n_rve), "slot out");
             A(cudaMalloc(&sl.d_it, sizeof(int64_t) * n_rve), "slot iters");
@@ -746,12 +856,13 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
             if (rc != FE2_OK) break;
         }
     }
-    for (int k = 0; k < 8 && rc == FE2_OK; ++k) {
+    const size_t ncls = std::max(b->classes_fp64.size(), b->classes_mixed.size());
+    for (size_t k = 0; k < ncls + 2 && rc == FE2_OK; ++k) {
         cudaEvent_t e;
         A(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
         if (rc == FE2_OK) b->ev.push_back(e);
     }
-    for (int k = 0; k < 24 && rc == FE2_OK; ++k) {
+    for (size_t k = 0; k < 6 * ncls + 8 && rc == FE2_OK; ++k) {
         cudaEvent_t e;
         A(cudaEventCreate(&e), "timing event");
         if (rc == FE2_OK) b->tev.push_back(e);
@@ -813,13 +924,12 @@ extern "C" fe2_status fe2_batch_plan(int32_t n_rve, const int64_t *node_off, con
         if (class_parts) class_parts[k] = c.parts;
         if (class_rves) class_rves[k] = (int32_t)c.rves.size();
         for (int lead = 1; lead >= 0; --lead) {
-            const size_t sm = lead ? mixed_lead_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit)
-                                   : mixed_fp32_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit);
-            const bool st = mixed_staged(lead, sm, c.part_max);
+            const size_t sm = class_smem(c, lead, limit);
+            const bool st = lead ? c.lead_staged : c.fp32_staged;
             const size_t at = 2 * k + (lead ? 0 : 1);
             if (smem) smem[at] = (int64_t)sm;
             if (staged) staged[at] = st ? 1 : 0;
-            if (block) block[at] = mixed_block(0, lead != 0, st);
+            if (block) block[at] = class_block(c, lead, 0);
         }
     }
     return FE2_OK;
@@ -837,16 +947,15 @@ fe2_status check_opts(const fe2_opts &o) {
     if (o.block_threads != 0 && (o.block_threads < 64 || o.block_threads > 512 || o.block_threads % 32))
         return fail(FE2_EINVAL, "block_threads must be 0 or a multiple of 32 in [64, 512]");
     if (!(o.lead_tol >= 0.0) || !std::isfinite(o.lead_tol)) return fail(FE2_EINVAL, "lead_tol must be finite and >= 0");
+    if (o.launch != 0 && o.launch != 1) return fail(FE2_EINVAL, "launch must be 0 (graph) or 1 (stream)");
     return FE2_OK;
 }
 
-// Threads per CTA of the mixed solver's kernels: 256 for the double-float lead
-// (two CTAs per SM keep more clusters resident), 512 for the FP32 kernel (more
-// warps to hide its latency chain). A fixed default keeps every RVE's result
-// independent of which other RVEs share its launch (partial sums follow the
-// thread mapping).
 // CTA size of a mixed launch: 512 threads, except the lead kernel without its
-// element table (256: two CTAs per SM, its registers allow no more).
+// element table (256: two CTAs per SM, its registers allow no more). The size
+// is a function of the RVE (its bucket's tuning) and never of the batch, which
+// keeps every RVE's result independent of which other RVEs share its launch
+// (partial sums follow the thread mapping).
 int mixed_block(int requested, bool lead, bool staged) {
     const int cap = lead && !staged ? 256 : 512;
     return requested ? std::min(requested, cap) : cap;
@@ -879,9 +988,24 @@ fe2_status reorder_queues(fe2_batch *b) {
 
 // Launch the solver kernels of one class on `s` for `nq` queued RVEs. Timing
 // events (tev) are recorded only when `timed` is non-null.
+int resident_of(fe2_batch *b, int kind, int parts, int block, size_t smem, int part_cap) {
+    const auto key = std::make_tuple(kind, parts, block, smem, part_cap);
+    auto it = b->occ.find(key);
+    if (it != b->occ.end()) return it->second;
+    const int r = kind == 2 ? occupancy_dr_fp64(parts, block, smem)
+                            : occupancy_dr_mixed(kind, parts, block, smem, part_cap);
+    b->occ[key] = r;
+    return r;
+}
+
+// Timing event around a launch: recorded as a graph node while capturing.
+cudaError_t record_timing(cudaEvent_t e, cudaStream_t s, bool capturing) {
+    return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
 fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, SolveParams P,
                         const int32_t *queue, int nq, int32_t *counters, cudaStream_t s, int *timed,
-                        int *launches) {
+                        int *launches, bool capturing = false) {
     const bool fp64 = o.precision == FE2_PREC_FP64;
     const DevMesh M = b->mesh();
     const DevState S = b->state();
@@ -893,38 +1017,41 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
     if (fp64) {
         const int block = o.block_threads ? o.block_threads : 512;
         const size_t smem = c.smem_positions ? c.smem_bytes : 0;
-        const int per_sm = std::max(1, occupancy_dr_fp64(c.smem_positions, block, smem));
+        const int per_sm = std::max(1, resident_of(b, 2, c.smem_positions, block, smem, 0));
         const int grid = std::max(1, std::min<int>(nq, per_sm * b->sm_count));
         if (timed) {
             if (*timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
-            CUDA_TRY(cudaEventRecord(b->tev[*timed], s));
+            CUDA_TRY(record_timing(b->tev[*timed], s, capturing));
         }
         const int e = launch_dr_fp64(M, S, R, P, grid, block, smem, s);
         if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
         if (timed) {
-            CUDA_TRY(cudaEventRecord(b->tev[*timed + 1], s));
+            CUDA_TRY(record_timing(b->tev[*timed + 1], s, capturing));
             *timed += 2;
         }
         ++*launches;
     } else {
-        for (int lead = 1; lead >= 0; --lead) {
+        // the double-float lead, the FP32 phase, and the double-float resume
+        // of RVEs whose FP32 phase stalled (a lead launch that skips the rest)
+        for (int step = 0; step < 3; ++step) {
+            const int lead = step == 1 ? 0 : 1;
+            P.resume = step == 2 ? 1 : 0;
             const size_t limit = b->smem_optin - 16384;
-            const size_t smem = lead ? mixed_lead_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit)
-                                     : mixed_fp32_smem(c.part_max, c.free_max, c.elem_max, c.slot_max, limit);
-            const int block = mixed_block(o.block_threads, lead != 0, mixed_staged(lead, smem, c.part_max));
-            const int resident = occupancy_dr_mixed(lead, c.parts, block, smem, c.part_max);
+            const size_t smem = class_smem(c, lead, limit);
+            const int block = class_block(c, lead, o.block_threads);
+            const int resident = resident_of(b, lead, c.parts, block, smem, c.part_max);
             if (resident < 1)
                 return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
                                            std::to_string(smem) + " B shared memory fits");
             if (timed) {
                 if (*timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
-                CUDA_TRY(cudaEventRecord(b->tev[*timed], s));
+                CUDA_TRY(record_timing(b->tev[*timed], s, capturing));
             }
             const int e = launch_dr_mixed(M, S, R, P, lead, std::min(nq, resident), c.parts, block, smem,
                                           c.part_max, c.free_max, c.elem_max, c.slot_max, s);
             if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
             if (timed) {
-                CUDA_TRY(cudaEventRecord(b->tev[*timed + 1], s));
+                CUDA_TRY(record_timing(b->tev[*timed + 1], s, capturing));
                 *timed += 2;
             }
             ++*launches;
@@ -944,30 +1071,126 @@ SolveParams make_params(fe2_batch *b, const fe2_opts &o) {
     P.lead_iters = o.lead_iters;
     P.lead_tol = o.lead_tol;
     P.rebase_every = o.rebase_every;
+    P.stall_window = o.stall_window == 0 ? 250000 : (o.stall_window < 0 ? 0 : o.stall_window);
+    P.resume = 0;
     return P;
 }
 
-fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
+// Serving submissions and batched solves share the per-RVE state (F, u,
+// results). A batched call orders its stream after every submission still in
+// flight (device-side wait), and a host readback waits for them; a submission
+// waits for the last batched solve (fe2_batch_submit).
+fe2_status after_slots(fe2_batch *b, cudaStream_t st) {
+    for (auto &sl : b->slots)
+        if (sl.busy) CUDA_TRY(cudaStreamWaitEvent(st, sl.done, 0));
+    return FE2_OK;
+}
+fe2_status wait_slots(fe2_batch *b) {
+    for (auto &sl : b->slots)
+        if (sl.busy) CUDA_TRY(cudaEventSynchronize(sl.done));
+    return FE2_OK;
+}
+
+// The launches of one batched solve, issued on `st`: reset the work-queue
+// heads, fork one stream per class, launch each class's persistent kernels,
+// join back on `st`.
+fe2_status record_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st, bool capturing, int *launches,
+                        int *timed) {
     const bool fp64 = o.precision == FE2_PREC_FP64;
     auto &classes = fp64 ? b->classes_fp64 : b->classes_mixed;
+    CUDA_TRY(cudaMemsetAsync(b->d_counters.p, 0, sizeof(int32_t) * kCountersPerClass * classes.size(), st));
+    const SolveParams P = make_params(b, o);
+    CUDA_TRY(cudaEventRecord(b->ev[0], st));
+    for (size_t k = 0; k < classes.size(); ++k) {
+        const SizeClass &c = classes[k];
+        cudaStream_t s = b->side[k % b->side.size()];
+        CUDA_TRY(cudaStreamWaitEvent(s, b->ev[0], 0));
+        const fe2_status r = launch_class(b, o, c, P, b->d_queue.p + (fp64 ? 0 : b->n_rve) + c.queue_off,
+                                          (int)c.rves.size(), b->d_counters.p + kCountersPerClass * k, s, timed, launches,
+                                          capturing);
+        if (r != FE2_OK) return r;
+        CUDA_TRY(cudaEventRecord(b->ev[1 + k], s));
+        CUDA_TRY(cudaStreamWaitEvent(st, b->ev[1 + k], 0));
+    }
+    return FE2_OK;
+}
+
+// Launch shapes (resident counts, kernel attributes) of every class, queried
+// before a capture so that the capture records launches only.
+fe2_status warm_shapes(fe2_batch *b, const fe2_opts &o) {
+    const bool fp64 = o.precision == FE2_PREC_FP64;
+    const size_t limit = b->smem_optin - 16384;
+    for (const SizeClass &c : fp64 ? b->classes_fp64 : b->classes_mixed) {
+        if (fp64) {
+            const int block = o.block_threads ? o.block_threads : 512;
+            resident_of(b, 2, c.smem_positions, block, c.smem_positions ? c.smem_bytes : 0, 0);
+            continue;
+        }
+        for (int lead = 1; lead >= 0; --lead) {
+            const size_t smem = class_smem(c, lead, limit);
+            if (smem > limit) {
+                int32_t big = c.rves.front();
+                for (int32_t p : c.rves) if (b->rve[p].n_nodes > b->rve[big].n_nodes) big = p;
+                return fail(FE2_EINVAL, "RVE " + std::to_string(big) + " (" +
+                                            std::to_string(b->rve[big].n_nodes) +
+                                            " nodes) exceeds the mixed solver's shared memory; use FE2_PREC_FP64");
+            }
+            if (resident_of(b, lead, c.parts, class_block(c, lead, o.block_threads), smem, c.part_max) < 1)
+                return fail(FE2_ECUDA, "no cluster of " + std::to_string(c.parts) + " CTAs with " +
+                                           std::to_string(smem) + " B shared memory fits");
+        }
+    }
+    return FE2_OK;
+}
+
+bool same_solve_opts(const fe2_opts &a, const fe2_opts &b) {
+    return a.tol == b.tol && a.max_iter == b.max_iter && a.dt_safety == b.dt_safety &&
+           a.precision == b.precision && a.init == b.init && a.kinetic_energy == b.kinetic_energy &&
+           a.block_threads == b.block_threads && a.lead_iters == b.lead_iters &&
+           a.rebase_every == b.rebase_every && a.lead_tol == b.lead_tol && a.stall_window == b.stall_window;
+}
+
+fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
     {
         const fe2_status r = reorder_queues(b);
         if (r != FE2_OK) return r;
     }
-    CUDA_TRY(cudaMemsetAsync(b->d_counters.p, 0, sizeof(int32_t) * 32, st));
-    const SolveParams P = make_params(b, o);
-    // fork: every class runs on its own stream, concurrently
-    CUDA_TRY(cudaEventRecord(b->ev[0], st));
-    int launches = 0, timed = 0;
-    for (size_t k = 0; k < classes.size(); ++k) {
-        const SizeClass &c = classes[k];
-        cudaStream_t s = b->side[k];
-        CUDA_TRY(cudaStreamWaitEvent(s, b->ev[0], 0));
-        const fe2_status r = launch_class(b, o, c, P, b->d_queue.p + (fp64 ? 0 : b->n_rve) + c.queue_off,
-                                          (int)c.rves.size(), b->d_counters.p + 2 * k, s, &timed, &launches);
+    {
+        const fe2_status r = warm_shapes(b, o);
         if (r != FE2_OK) return r;
-        CUDA_TRY(cudaEventRecord(b->ev[1 + k], s));
-        CUDA_TRY(cudaStreamWaitEvent(st, b->ev[1 + k], 0));
+    }
+    int launches = 0, timed = 0;
+    if (o.launch == 1) {
+        const fe2_status r = record_solve(b, o, st, false, &launches, &timed);
+        if (r != FE2_OK) return r;
+    } else {
+        // one CUDA graph per option set: captured on the first solve with
+        // these options, replayed by every later one
+        if (!b->graph || !same_solve_opts(b->graph_opts, o)) {
+            if (b->graph) CUDA_TRY(cudaGraphExecDestroy(b->graph));
+            b->graph = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            const fe2_status r = record_solve(b, o, b->cap, true, &launches, &timed);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+            if (r != FE2_OK) {
+                if (g) cudaGraphDestroy(g);
+                return r;
+            }
+            if (e != cudaSuccess) return fail(FE2_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                b->graph = nullptr;
+                return fail(FE2_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+            }
+            b->graph_opts = o;
+            b->graph_launches = launches;
+            b->graph_timed = timed;
+        }
+        CUDA_TRY(cudaGraphLaunch(b->graph, st));
+        launches = b->graph_launches;
+        timed = b->graph_timed;
     }
     b->last_launches = launches;
     b->last_timed = timed / 2;
@@ -987,6 +1210,8 @@ extern "C" fe2_status fe2_batch_solve_dev(fe2_batch *b, const double *F_dev, con
     fe2_status s = check_opts(o);
     if (s != FE2_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s = after_slots(b, st);
+    if (s != FE2_OK) return s;
     CUDA_TRY(cudaMemcpyAsync(b->d_F.p, F_dev, sizeof(double) * 9 * b->n_rve,
                              cudaMemcpyDeviceToDevice, st));
     return launch_solve(b, o, st);
@@ -1003,6 +1228,8 @@ extern "C" fe2_status fe2_batch_solve(fe2_batch *b, const double *F, const fe2_o
     // Stage F in pinned memory so the caller's buffer is free on return; the
     // previous solve's upload from the staging buffer must have completed.
     CUDA_TRY(cudaEventSynchronize(b->ev_F));
+    s = after_slots(b, st);
+    if (s != FE2_OK) return s;
     std::memcpy(b->h_F, F, sizeof(double) * 9 * b->n_rve);
     CUDA_TRY(cudaMemcpyAsync(b->d_F.p, b->h_F, sizeof(double) * 9 * b->n_rve, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaEventRecord(b->ev_F, st));
@@ -1014,6 +1241,10 @@ extern "C" fe2_status fe2_batch_stress(fe2_batch *b, double *sigma, int64_t *ite
     if (!b) return fail(FE2_EINVAL, "NULL batch");
     if (!b->solved) return fail(FE2_ESTATE, "no solve has been issued");
     CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    {
+        const fe2_status w = wait_slots(b);
+        if (w != FE2_OK) return w;
+    }
     const size_t P = b->n_rve;
     if (sigma) CUDA_TRY(cudaMemcpy(sigma, b->d_sigma.p, sizeof(double) * 9 * P, cudaMemcpyDeviceToHost));
     if (iters) CUDA_TRY(cudaMemcpy(iters, b->d_iters.p, sizeof(int64_t) * P, cudaMemcpyDeviceToHost));
@@ -1027,6 +1258,10 @@ extern "C" fe2_status fe2_batch_diagnostics(fe2_batch *b, double *f_ref, double 
     if (!b) return fail(FE2_EINVAL, "NULL batch");
     if (!b->solved) return fail(FE2_ESTATE, "no solve has been issued");
     CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    {
+        const fe2_status w = wait_slots(b);
+        if (w != FE2_OK) return w;
+    }
     const size_t P = b->n_rve;
     if (f_ref) CUDA_TRY(cudaMemcpy(f_ref, b->d_fref.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
     if (kinetic_energy) CUDA_TRY(cudaMemcpy(kinetic_energy, b->d_ke.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
@@ -1039,6 +1274,11 @@ extern "C" fe2_status fe2_batch_results_dev(fe2_batch *b, double *sigma_dev, int
     if (!b) return fail(FE2_EINVAL, "NULL batch");
     if (!b->solved) return fail(FE2_ESTATE, "no solve has been issued");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamWaitEvent(st, b->ev_done, 0));
+    {
+        const fe2_status w = after_slots(b, st);
+        if (w != FE2_OK) return w;
+    }
     const size_t P = b->n_rve;
     if (sigma_dev) CUDA_TRY(cudaMemcpyAsync(sigma_dev, b->d_sigma.p, sizeof(double) * 9 * P, cudaMemcpyDeviceToDevice, st));
     if (iters_dev) CUDA_TRY(cudaMemcpyAsync(iters_dev, b->d_iters.p, sizeof(int64_t) * P, cudaMemcpyDeviceToDevice, st));
@@ -1050,6 +1290,10 @@ extern "C" fe2_status fe2_batch_results_dev(fe2_batch *b, double *sigma_dev, int
 extern "C" fe2_status fe2_batch_get_displacement(fe2_batch *b, double *u) {
     if (!b || !u) return fail(FE2_EINVAL, "NULL batch or u");
     if (b->solved) CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    {
+        const fe2_status w = wait_slots(b);
+        if (w != FE2_OK) return w;
+    }
     const int64_t N = b->n_nodes;
     std::vector<double> h(3 * N);
     CUDA_TRY(cudaMemcpy(h.data(), b->d_u.p, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost));
@@ -1066,6 +1310,10 @@ extern "C" fe2_status fe2_batch_set_displacement(fe2_batch *b, const double *u) 
     for (int64_t k = 0; k < 3 * N; ++k)
         if (!std::isfinite(u[k])) return fail(FE2_EINVAL, "non-finite displacement");
     if (b->solved) CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    {
+        const fe2_status w = wait_slots(b);
+        if (w != FE2_OK) return w;
+    }
     std::vector<double> h(3 * N);
     for (int64_t k = 0; k < N; ++k) {
         const int64_t o = b->perm_to_orig[k];
@@ -1122,6 +1370,9 @@ extern "C" fe2_status fe2_batch_solve_naive(fe2_batch *b, const double *F, const
     int64_t nmax = 0;
     for (auto &R : b->rve) nmax = std::max<int64_t>(nmax, R.n_nodes);
     if (!b->d_naive.p) CUDA_TRY(b->d_naive.alloc(6 * nmax + 16));
+    CUDA_TRY(cudaStreamWaitEvent(st, b->ev_done, 0));
+    s = after_slots(b, st);
+    if (s != FE2_OK) return s;
     CUDA_TRY(cudaMemcpyAsync(b->d_F.p, F, sizeof(double) * 9 * b->n_rve, cudaMemcpyHostToDevice, st));
     NaiveScratch W;
     W.x = b->d_naive.p;
@@ -1228,17 +1479,23 @@ extern "C" fe2_status fe2_batch_submit(fe2_batch *b, int32_t n, const int32_t *r
     }
     std::memcpy(sl.h_F, F, sizeof(double) * 9 * n);
     cudaStream_t s = sl.stream;
+    // after the last batched solve, which writes every RVE's state
+    CUDA_TRY(cudaStreamWaitEvent(s, b->ev_done, 0));
     CUDA_TRY(cudaMemcpyAsync(sl.d_ids, sl.h_ids, sizeof(int32_t) * 2 * n, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(sl.d_F, sl.h_F, sizeof(double) * 9 * n, cudaMemcpyHostToDevice, s));
     k_scatter_F<<<(9 * n + 255) / 256, 256, 0, s>>>(n, sl.d_ids, sl.d_F, b->d_F.p);
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaMemsetAsync(sl.d_cnt, 0, sizeof(int32_t) * 32, s));
+    CUDA_TRY(cudaMemsetAsync(sl.d_cnt, 0, sizeof(int32_t) * kCountersPerClass * classes.size(), s));
+    {
+        const fe2_status r = warm_shapes(b, o);
+        if (r != FE2_OK) return r;
+    }
     const SolveParams P = make_params(b, o);
     int launches = 0;
     for (auto &[c, q0] : starts) {
         if (per[c].empty()) continue;
         const fe2_status r = launch_class(b, o, classes[c], P, sl.d_ids + q0, (int)per[c].size(),
-                                          sl.d_cnt + 2 * c, s, nullptr, &launches);
+                                          sl.d_cnt + kCountersPerClass * c, s, nullptr, &launches);
         if (r != FE2_OK) return r;
     }
     k_gather_results<<<(n + 127) / 128, 128, 0, s>>>(n, sl.d_ids, b->d_sigma.p, b->d_rel.p, b->d_iters.p,
@@ -1368,5 +1625,290 @@ extern "C" fe2_status fe2_serve(fe2_batch *b, int32_t n_req, const int32_t *rve,
         }
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    return FE2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch tuning and the autotuner (Section III: the best number of threads
+// per team depends on the sub-problem size). A configuration per size bucket:
+// cluster size and FP32-kernel CTA size, chosen by timing bounded solves.
+// ---------------------------------------------------------------------------
+namespace {
+
+fe2_status check_tuning(const fe2_tuning &t) {
+    for (int k = 0; k < 32; ++k) {
+        const int c = t.parts[k];
+        if (c < 0 || c > kMaxParts || (c & (c - 1)) != 0) return fail(FE2_EINVAL, "tuning: parts must be 0 or a power of two <= 16");
+        for (int v : {t.block_fp32[k], t.block_lead[k]})
+            if (v != 0 && (v < 64 || v > 512 || v % 32)) return fail(FE2_EINVAL, "tuning: CTA sizes must be 0 or multiples of 32 in [64, 512]");
+    }
+    return FE2_OK;
+}
+
+// The value of "key": <number> inside text[lo, hi), or NAN.
+double json_num(const std::string &text, size_t lo, size_t hi, const char *key) {
+    const std::string k = std::string("\"") + key + "\"";
+    const size_t at = text.find(k, lo);
+    if (at == std::string::npos || at >= hi) return NAN;
+    size_t c = text.find(':', at + k.size());
+    if (c == std::string::npos || c >= hi) return NAN;
+    return std::strtod(text.c_str() + c + 1, nullptr);
+}
+std::string json_str(const std::string &text, const char *key) {
+    const std::string k = std::string("\"") + key + "\"";
+    const size_t at = text.find(k);
+    if (at == std::string::npos) return "";
+    const size_t q0 = text.find('"', text.find(':', at + k.size()));
+    if (q0 == std::string::npos) return "";
+    const size_t q1 = text.find('"', q0 + 1);
+    return q1 == std::string::npos ? "" : text.substr(q0 + 1, q1 - q0 - 1);
+}
+
+struct DeviceId {
+    std::string name;
+    int sms = 0;
+};
+fe2_status device_id(DeviceId &d) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    d.name = prop.name;
+    d.sms = prop.multiProcessorCount;
+    return FE2_OK;
+}
+
+}  // namespace
+
+extern "C" fe2_status fe2_tuning_set(const fe2_tuning *t) {
+    if (!t) {
+        g_tuning = fe2_tuning{};
+        return FE2_OK;
+    }
+    const fe2_status s = check_tuning(*t);
+    if (s != FE2_OK) return s;
+    g_tuning = *t;
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_tuning_get(fe2_tuning *t) {
+    if (!t) return fail(FE2_EINVAL, "NULL tuning");
+    *t = g_tuning;
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_tuning_load(const char *path) {
+    if (!path) return fail(FE2_EINVAL, "NULL path");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(FE2_EINVAL, std::string("cannot read ") + path);
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+    std::fclose(f);
+    DeviceId d;
+    const fe2_status ds = device_id(d);
+    if (ds != FE2_OK) return ds;
+    if (json_str(text, "gpu") != d.name || (int)json_num(text, 0, text.size(), "sm_count") != d.sms)
+        return fail(FE2_EINVAL, std::string("tuning file ") + path + " was measured on another GPU");
+    if (json_str(text, "precision") != "mixed") return fail(FE2_EINVAL, "tuning file is not for the mixed solver");
+    fe2_tuning t = {};
+    const size_t arr = text.find("\"buckets\"");
+    if (arr == std::string::npos) return fail(FE2_EINVAL, "tuning file has no buckets");
+    // every object after the key is one bucket (objects hold no nested objects)
+    size_t pos = arr;
+    while (true) {
+        const size_t o0 = text.find('{', pos);
+        if (o0 == std::string::npos) break;
+        const size_t o1 = text.find('}', o0);
+        if (o1 == std::string::npos) return fail(FE2_EINVAL, "tuning file is malformed");
+        const double b = json_num(text, o0, o1, "bucket"), c = json_num(text, o0, o1, "parts"),
+                     k = json_num(text, o0, o1, "block_fp32");
+        if (!(b >= 0 && b < 32) || std::isnan(c) || std::isnan(k)) return fail(FE2_EINVAL, "tuning file is malformed");
+        t.parts[(int)b] = (int32_t)c;
+        t.block_fp32[(int)b] = (int32_t)k;
+        pos = o1 + 1;
+    }
+    return fe2_tuning_set(&t);
+}
+
+extern "C" fe2_status fe2_autotune(int32_t n_rve, const int64_t *node_off, const double *X,
+                                   const int64_t *elem_off, const int32_t *conn, const double *EA,
+                                   const uint8_t *fixed, const double *damping, const double *F,
+                                   int64_t trial_iters, const char *json_path, fe2_tuning *out) {
+    {
+        const fe2_status v = validate_batch(n_rve, node_off, X, elem_off, conn, EA, fixed, nullptr, damping);
+        if (v != FE2_OK) return v;
+    }
+    if (!F) return fail(FE2_EINVAL, "NULL F");
+    if (trial_iters < 8) return fail(FE2_EINVAL, "trial_iters must be >= 8");
+    DeviceId dev;
+    {
+        const fe2_status ds = device_id(dev);
+        if (ds != FE2_OK) return ds;
+    }
+    int devi = 0;
+    CUDA_TRY(cudaGetDevice(&devi));
+    size_t optin = 0;
+    {
+        cudaDeviceProp prop;
+        CUDA_TRY(cudaGetDeviceProperties(&prop, devi));
+        optin = prop.sharedMemPerBlockOptin;
+    }
+    const int target = std::max(64, env_int("FE2_NODES_PER_CTA", 1024));
+    const fe2_tuning saved = g_tuning;
+    fe2_tuning best = saved;
+    std::vector<std::vector<int32_t>> by_bucket(32);
+    for (int32_t p = 0; p < n_rve; ++p) by_bucket[node_bucket((int)(node_off[p + 1] - node_off[p]))].push_back(p);
+    cudaStream_t st = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&t0));
+    CUDA_TRY(cudaEventCreate(&t1));
+    std::string report;
+    fe2_status rc = FE2_OK;
+    for (int bk = 0; bk < 32 && rc == FE2_OK; ++bk) {
+        const auto &S = by_bucket[bk];
+        if (S.empty()) continue;
+        int cmin = 1;
+        for (int32_t p : S) cmin = std::max(cmin, min_parts((int)(node_off[p + 1] - node_off[p]), target, optin - 16384));
+        double best_rate = -1.0;
+        int best_c = 0, best_blk = 0;
+        std::string tried;
+        for (int C = cmin; C <= kMaxParts && rc == FE2_OK; C *= 2) {
+            // the bucket's samples, replicated until they fill every SM once
+            const int want = std::max<int>((int)S.size(), (dev.sms + C - 1) / C);
+            std::vector<int64_t> no(1, 0), eo(1, 0);
+            std::vector<double> x, ea, damp, f;
+            std::vector<int32_t> cn;
+            std::vector<uint8_t> fx;
+            for (int k = 0; k < want; ++k) {
+                const int32_t p = S[k % S.size()];
+                const int64_t n0 = node_off[p], n1 = node_off[p + 1], e0 = elem_off[p], e1 = elem_off[p + 1];
+                x.insert(x.end(), X + 3 * n0, X + 3 * n1);
+                fx.insert(fx.end(), fixed + n0, fixed + n1);
+                cn.insert(cn.end(), conn + 2 * e0, conn + 2 * e1);
+                ea.insert(ea.end(), EA + e0, EA + e1);
+                damp.push_back(damping ? damping[p] : 0.002 * std::cbrt(512.0 / (double)(n1 - n0)));
+                f.insert(f.end(), F + 9 * (int64_t)p, F + 9 * (int64_t)p + 9);
+                no.push_back(no.back() + (n1 - n0));
+                eo.push_back(eo.back() + (e1 - e0));
+            }
+            g_tuning = saved;
+            g_tuning.parts[bk] = C;
+            g_tuning.block_fp32[bk] = 0;
+            fe2_batch *tb = nullptr;
+            fe2_status cs = fe2_batch_create(want, no.data(), x.data(), eo.data(), cn.data(), ea.data(), fx.data(),
+                                             nullptr, damp.data(), st, &tb);
+            if (cs != FE2_OK) {
+                if (cs == FE2_ENOMEM) break;
+                rc = cs;
+                break;
+            }
+            bool forced_ok = true;
+            for (int32_t p = 0; p < want; ++p) forced_ok &= tb->rve[p].n_parts == C;
+            for (int blk : {256, 384, 512}) {
+                if (!forced_ok) break;
+                for (auto &c : tb->classes_mixed) c.block_fp32 = blk;
+                fe2_opts o;
+                fe2_opts_default(&o);
+                o.tol = 0.0;
+                o.launch = 1;
+                o.max_iter = 16;  // warm-up: attributes, occupancy
+                o.lead_iters = 4;
+                fe2_status ss = fe2_batch_solve(tb, f.data(), &o, st);
+                if (ss == FE2_OK) ss = fe2_batch_stress(tb, nullptr, nullptr, nullptr, nullptr);
+                if (ss != FE2_OK) {
+                    if (ss == FE2_EINVAL) break;  // does not fit this cluster size
+                    rc = ss;
+                    break;
+                }
+                o.max_iter = trial_iters;
+                o.lead_iters = trial_iters / 4;
+                CUDA_TRY(cudaEventRecord(t0, st));
+                ss = fe2_batch_solve(tb, f.data(), &o, st);
+                if (ss != FE2_OK) { rc = ss; break; }
+                CUDA_TRY(cudaEventRecord(t1, st));
+                CUDA_TRY(cudaEventSynchronize(t1));
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, t0, t1));
+                std::vector<int64_t> it(want);
+                ss = fe2_batch_stress(tb, nullptr, it.data(), nullptr, nullptr);
+                if (ss != FE2_OK) { rc = ss; break; }
+                double work = 0.0;
+                for (int32_t p = 0; p < want; ++p) work += (double)(no[p + 1] - no[p]) * (double)it[p];
+                const double used = std::min<double>(dev.sms, (double)want * C);
+                const double rate = work / (ms * 1e-3) / used;
+                char line[96];
+                std::snprintf(line, sizeof line, "%s[%d, %d, %.6g]", tried.empty() ? "" : ", ", C, blk, rate);
+                tried += line;
+                if (rate > best_rate) { best_rate = rate; best_c = C; best_blk = blk; }
+            }
+            fe2_batch_destroy(tb);
+        }
+        if (rc != FE2_OK) break;
+        if (best_c > 0) {
+            best.parts[bk] = best_c;
+            best.block_fp32[bk] = best_blk;
+            char line[256];
+            std::snprintf(line, sizeof line,
+                          "%s  {\"bucket\": %d, \"nodes_lo\": %lld, \"nodes_hi\": %lld, \"samples\": %zu, "
+                          "\"parts\": %d, \"block_fp32\": %d, \"node_iters_per_s_per_sm\": %.6g, \"tried\": [",
+                          report.empty() ? "" : ",\n", bk, (long long)1 << bk, ((long long)2 << bk) - 1, S.size(),
+                          best_c, best_blk, best_rate);
+            report += line;
+            report += tried + "]}";
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaStreamDestroy(st);
+    g_tuning = saved;
+    if (rc != FE2_OK) return rc;
+    g_tuning = best;
+    if (out) *out = best;
+    if (json_path) {
+        FILE *f = std::fopen(json_path, "wb");
+        if (!f) return fail(FE2_EINVAL, std::string("cannot write ") + json_path);
+        std::fprintf(f,
+                     "{\"gpu\": \"%s\", \"sm_count\": %d, \"precision\": \"mixed\", \"trial_iters\": %lld,\n"
+                     " \"objective\": \"node-iterations per second per SM over bounded solves\",\n"
+                     " \"tried_columns\": [\"parts\", \"block_fp32\", \"node_iters_per_s_per_sm\"],\n"
+                     " \"buckets\": [\n%s\n]}\n",
+                     dev.name.c_str(), dev.sms, (long long)trial_iters, report.c_str());
+        std::fclose(f);
+    }
+    return FE2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sharding over GPUs (Section I: the microscale problems are independent).
+// Longest-processing-time-first assignment of RVEs to ranks by estimated cost;
+// the only exchange is gathering the 9-double stresses afterwards.
+// ---------------------------------------------------------------------------
+extern "C" fe2_status fe2_shard_plan(int32_t n_rve, const int64_t *node_off, const int64_t *iters,
+                                     int32_t n_ranks, int32_t *rank_of, double *rank_cost) {
+    if (n_rve < 0 || !node_off || n_ranks < 1 || (n_rve > 0 && !rank_of))
+        return fail(FE2_EINVAL, "NULL argument, n_rve < 0 or n_ranks < 1");
+    std::vector<double> cost(n_rve);
+    for (int32_t p = 0; p < n_rve; ++p) {
+        const double n = (double)(node_off[p + 1] - node_off[p]);
+        if (!(n > 0)) return fail(FE2_EINVAL, "RVE " + std::to_string(p) + " has no nodes");
+        // measured iterations when given, else the growth of the iteration
+        // count with size seen on kNN networks (about n^0.5), so cost ~ n^1.5
+        cost[p] = iters && iters[p] > 0 ? n * (double)iters[p] : n * std::sqrt(n);
+    }
+    std::vector<int32_t> order(n_rve);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    std::vector<double> load(n_ranks, 0.0);
+    for (int32_t p : order) {
+        int32_t r = 0;
+        for (int32_t k = 1; k < n_ranks; ++k)
+            if (load[k] < load[r]) r = k;
+        rank_of[p] = r;
+        load[r] += cost[p];
+    }
+    if (rank_cost) std::copy(load.begin(), load.end(), rank_cost);
     return FE2_OK;
 }

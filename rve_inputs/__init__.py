@@ -281,6 +281,15 @@ def uneven_sizes(count: int, lo: int, hi: int, workload: int) -> np.ndarray:
                              count, lo, hi)
 
 
+def stratified_idx(sizes, k: int) -> list:
+    """k RVE indices spread evenly over the size order (smallest to largest):
+    the seeded, size-stratified subset on which the oracle checks and times
+    the uneven workloads."""
+    order = np.argsort(np.asarray(sizes), kind="stable")
+    pick = np.rint(np.linspace(0, len(order) - 1, k)).astype(int)
+    return sorted(int(order[i]) for i in pick)
+
+
 def serving_F(S: np.ndarray, step: int) -> np.ndarray:
     """F of a Gauss point at macro step ``step``: diag(1+0.005 step,1,1)(I+0.02 S)."""
     return np.diag([1.0 + 0.005 * step, 1.0, 1.0]) @ (np.eye(3) + 0.02 * S)

@@ -88,3 +88,34 @@ def test_request_loop_with_warm_restarts_matches_replay():
                 res = _drain(b2, 1)[p]
                 assert res[1] == out["iters"][r]
                 assert np.array_equal(res[0], out["sigma"][r])
+
+
+def test_batched_and_served_calls_are_ordered():
+    """A warm submission issued right after an asynchronous batched solve
+    starts from that solve's result, and a batched solve issued while
+    submissions are in flight starts after them: both give exactly the
+    serialised results."""
+    w = _workload([300, 900, 500], seed=35)
+    F2 = np.array([np.diag([1.005, 1.0, 1.0]) @ f for f in w.F])
+    # serialised order
+    with Batch(w.nets, damping=w.damping) as b:
+        b.solve(w.F, precision="fp64")
+        b.stress()  # waits
+        assert b.submit([1], F2[[1]], precision="fp64", init="warm") is not None
+        ser_warm = _drain(b, 1)[1]
+        assert b.submit([0, 2], w.F[[0, 2]], precision="fp64") is not None
+        _drain(b, 2)
+        b.solve(F2, precision="fp64", init="warm")
+        ser_batch = b.stress()
+    # the same calls without waiting in between
+    with Batch(w.nets, damping=w.damping) as b:
+        b.solve(w.F, precision="fp64")
+        assert b.submit([1], F2[[1]], precision="fp64", init="warm") is not None
+        got_warm = _drain(b, 1)[1]
+        assert b.submit([0, 2], w.F[[0, 2]], precision="fp64") is not None
+        b.solve(F2, precision="fp64", init="warm")  # while [0, 2] may be in flight
+        got_batch = b.stress()
+        _drain(b, 2)
+    assert got_warm[1] == ser_warm[1] and np.array_equal(got_warm[0], ser_warm[0])
+    assert np.array_equal(got_batch["iters"], ser_batch["iters"])
+    assert np.array_equal(got_batch["sigma"], ser_batch["sigma"])

@@ -1,7 +1,9 @@
 """The host-side packing of fe2_batch_create, read back through the host-only
 fe2_batch_layout (no GPU needed), against its documented invariants:
 
-- parts per RVE follow the cluster-size rule;
+- parts per RVE follow the cluster-size rule: the smallest power of two
+  whose parts hold the plain node state, doubled while the FP32 kernel's
+  element table does not fit;
 - the node permutation keeps each RVE's range, puts free nodes first part by
   part (degree order inside a part) and then fixed nodes part by part;
 - RCB parts have equal sizes to within one node;
@@ -15,10 +17,10 @@ import pytest
 import rve_inputs as ri
 
 SMEM_OPTIN = 232448       # GB300 opt-in shared memory per block
-NODE_BYTES = 120          # FP32 kernel bytes per staged node (bounds the part size)
+NODE_BYTES = 96           # FP32 kernel bytes per node without its element table
 
 
-def _expected_parts(n, target, smem_optin=SMEM_OPTIN):
+def _min_parts(n, target, smem_optin=SMEM_OPTIN):
     cap = smem_optin - 16384
     C = 1
     while C < 16 and (-(-n // C) > target or NODE_BYTES * (-(-n // C) + 64) > cap):
@@ -26,12 +28,33 @@ def _expected_parts(n, target, smem_optin=SMEM_OPTIN):
     return C
 
 
+def _check_parts(nets, target, L, smem_optin=SMEM_OPTIN):
+    """At least the minimal cluster; more only where the minimal one leaves
+    the FP32 kernel without its element table (checked through the plan with
+    the part count forced one step lower)."""
+    import paper_2305_07030_gb300 as m
+    for p, net in enumerate(nets):
+        C, C0 = int(L["parts"][p]), _min_parts(net.n_nodes, target, smem_optin)
+        assert C >= C0 and C & (C - 1) == 0 and C <= 16, (p, C, C0)
+        P = m.plan([net], smem_optin=smem_optin, nodes_per_cta=target)
+        if C < 16:
+            assert P["staged"][0, 1] == 1, (p, C)
+        if C > C0:
+            b = int(np.floor(np.log2(net.n_nodes)))
+            m.tuning_set({b: (C // 2, 0)})
+            try:
+                half = m.plan([net], smem_optin=smem_optin, nodes_per_cta=target)
+            finally:
+                m.tuning_set(None)
+            assert list(half["parts"]) == [C // 2]
+            assert half["staged"][0, 1] == 0, (p, C)
+
+
 def _check(nets, target, L):
     node_off, elem_off = L["node_off"], L["elem_off"]
     for p, net in enumerate(nets):
         base, n = int(node_off[p]), net.n_nodes
         C = int(L["parts"][p])
-        assert C == _expected_parts(n, target), (p, n, C)
         adj = [[] for _ in range(n)]
         for a, b in net.elems:
             adj[a].append(b)
@@ -84,6 +107,7 @@ def test_uneven_batch(target):
     import paper_2305_07030_gb300 as m
     L = m.layout(nets, nodes_per_cta=target)
     _check(nets, target or 1024, L)
+    _check_parts(nets, target or 1024, L)
 
 
 def test_isolated_node_is_held_fixed():
@@ -106,7 +130,29 @@ def test_smem_bounds_the_part_size():
     nets = _nets([3000], seed=33)
     small = 16384 + NODE_BYTES * (800 + 64)
     L = m.layout(nets, smem_optin=small, nodes_per_cta=4096)
-    assert int(L["parts"][0]) == _expected_parts(3000, 4096, small) == 4
+    assert _min_parts(3000, 4096, small) == 4
+    _check_parts(nets, 4096, L, smem_optin=small)
+
+
+def test_tuned_part_count_is_used_and_bounded():
+    """A tuned cluster size for a size bucket is used when feasible; one
+    below the minimal cluster is ignored."""
+    import paper_2305_07030_gb300 as m
+    nets = _nets([5000, 700], seed=35)
+    try:
+        m.tuning_set({12: (16, 256)})       # 4096 <= n < 8192
+        L = m.layout(nets)
+        assert list(L["parts"]) == [16, int(m.layout(nets[1:])["parts"][0])]
+        _check(nets, 1024, L)
+        m.tuning_set({12: (2, 0)})          # below the minimal 8 parts: ignored
+        assert int(m.layout(nets[:1])["parts"][0]) == 8
+        with pytest.raises(m.FE2Error, match="power of two"):
+            m.tuning_set({12: (3, 0)})
+        with pytest.raises(m.FE2Error, match="multiples of 32"):
+            m.tuning_set({12: (4, 100)})
+    finally:
+        m.tuning_set(None)
+    assert m.tuning_get() == {}
 
 
 def test_rejects_tiny_shared_memory():

@@ -32,10 +32,16 @@ def test_plan_is_consistent_with_the_layout(target):
     L = m.layout(nets, smem_optin=SMEM_OPTIN, nodes_per_cta=target)
     k = P["n_classes"]
     assert sum(P["rves"]) == len(nets)
-    # one class per cluster size, and every RVE in the class of its size
-    assert len(set(P["parts"].tolist())) == k
+    # every RVE in a class of its own cluster size; a class is one cluster
+    # size and one choice of element tables for each kernel
     for p in range(len(nets)):
         assert P["parts"][P["rve_class"][p]] == L["parts"][p]
+    keys = [(int(P["parts"][c]), *map(int, P["staged"][c])) for c in range(k)]
+    for c in range(k):
+        for p in np.nonzero(P["rve_class"] == c)[0]:
+            alone = m.plan([nets[p]], smem_optin=SMEM_OPTIN, nodes_per_cta=target)
+            assert (int(alone["parts"][0]), *map(int, alone["staged"][0])) == keys[c]
+            assert alone["block"].tolist() == [P["block"][c].tolist()]
     assert np.bincount(P["rve_class"], minlength=k).tolist() == P["rves"].tolist()
     # every launch fits the shared-memory budget; the lead kernel without its
     # table runs 256 threads per CTA, everything else 512
@@ -46,9 +52,9 @@ def test_plan_is_consistent_with_the_layout(target):
         assert P["block"][c, 1] == 512
 
 
-def test_small_shared_memory_moves_classes_off_the_tables():
-    """With less shared memory the same RVEs need more parts or lose their
-    element tables; a plan never exceeds the budget."""
+def test_small_shared_memory_needs_more_parts():
+    """With less shared memory the same RVEs need at least as many parts;
+    a plan never exceeds the budget."""
     import paper_2305_07030_gb300 as m
     rng = np.random.default_rng(42)
     nets = [ri.random_network(int(n), rng) for n in (800, 1600)]
@@ -56,16 +62,20 @@ def test_small_shared_memory_moves_classes_off_the_tables():
     small_optin = 120 * 1000
     small = m.plan(nets, smem_optin=small_optin)
     assert (small["smem"] <= small_optin - 16384).all()
-    assert small["staged"].sum() <= big["staged"].sum()
+    for p in range(len(nets)):
+        assert small["parts"][small["rve_class"][p]] >= big["parts"][big["rve_class"][p]]
 
 
 def test_mixed_path_size_limit():
-    """The mixed solver holds each part's node state in shared memory (120 B
-    per node), so on a GB300 an RVE fits in 16 parts of at most 1800 nodes:
-    28,800 nodes fit, 28,801 do not (the limit stated for FE2_PREC_MIXED)."""
+    """The mixed solver holds each part's node state in shared memory (96 B
+    per node without the element table), so on a GB300 an RVE fits in 16
+    parts of at most 2,250 nodes; the bisection leaves parts within one node
+    of each other, so 36,000 nodes fit and 36,017 do not. The header states
+    the guaranteed 34,976 (parts of 2,186 with slack for the bisection)."""
     import paper_2305_07030_gb300 as m
     budget = SMEM_OPTIN - 16384
-    for n, fits in ((28_800, True), (28_801, False)):
+    assert budget // 96 == 2250
+    for n, fits in ((34_976, True), (36_000, True), (36_017, False)):
         P = m.plan([ri.random_network(n, np.random.default_rng(43))], smem_optin=SMEM_OPTIN)
         assert list(P["parts"]) == [16]
         assert bool((P["smem"] <= budget).all()) == fits, (n, P["smem"].tolist())
