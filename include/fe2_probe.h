@@ -11,6 +11,16 @@
  *   sm_clock_mhz  out (may be NULL): the device's maximum SM clock
  * Returns 0, 1 for a NULL gbs, 2 if the scratch allocation fails, 3 on a CUDA
  * error. Allocates and frees its own scratch; synchronous.
+ *
+ * fe2_probe_fp64_rates: aggregate FP64 throughput of the current device for
+ * the operations of the FP64 relaxation kernel, whose arithmetic is IEEE
+ * double with explicit rounding: fused multiply-add (the rate of a plain add
+ * or multiply), correctly rounded division and correctly rounded square root.
+ * Each is timed on 8 independent dependency chains per thread, 8 CTAs of 256
+ * threads per SM (best of 5 launches, CUDA events).
+ *   fma_per_s, div_per_s, sqrt_per_s  out: operations per second, all SMs
+ * Returns 0, 1 for a NULL pointer, 2 if the scratch allocation fails, 3 on a
+ * CUDA error. Allocates and frees its own scratch; synchronous.
  */
 #ifndef FE2_PROBE_H
 #define FE2_PROBE_H
@@ -18,6 +28,7 @@
 extern "C" {
 #endif
 int fe2_probe_smem_bandwidth(double *gbs, double *sm_clock_mhz);
+int fe2_probe_fp64_rates(double *fma_per_s, double *div_per_s, double *sqrt_per_s);
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ def _load():
     lib.fe2_tuning_load.argtypes = [C.c_char_p]
     lib.fe2_autotune.argtypes = [I32, P, P, P, P, P, P, P, P, I64, C.c_char_p, C.POINTER(Tuning)]
     lib.fe2_shard_plan.argtypes = [I32, P, P, I32, P, P]
+    lib.fe2_batch_energy.argtypes = [P, P, P, P, P]
     lib.fe2_last_error.argtypes = []
     lib.fe2_last_error.restype = C.c_char_p
     for name in ("fe2_batch_create", "fe2_batch_solve", "fe2_batch_solve_dev",
@@ -94,7 +95,7 @@ def _load():
                  "fe2_batch_diagnostics", "fe2_batch_parts", "fe2_batch_submit",
                  "fe2_batch_poll", "fe2_serve", "fe2_batch_layout", "fe2_batch_plan",
                  "fe2_tuning_set", "fe2_tuning_get", "fe2_tuning_load", "fe2_autotune",
-                 "fe2_shard_plan"):
+                 "fe2_shard_plan", "fe2_batch_energy"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -217,7 +218,8 @@ def make_opts(tol=1e-8, max_iter=10_000_000, dt_safety=0.9, precision="mixed", i
     o.dt_safety = float(dt_safety)
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
     o.init = _INIT[init] if isinstance(init, str) else int(init)
-    o.kinetic_energy = int(bool(kinetic_energy))
+    # True / 1: kinetic energy; "balance" / 2: also the energy-balance work terms
+    o.kinetic_energy = 2 if kinetic_energy in ("balance", 2) else int(bool(kinetic_energy))
     o.block_threads = int(block_threads)
     o.lead_iters = int(lead_iters)
     o.rebase_every = int(rebase_every)
@@ -376,6 +378,16 @@ class Batch:
     def set_displacement(self, u):
         uh = np.ascontiguousarray(u, np.float64).reshape(self.n_nodes, 3)
         _check(_lib.fe2_batch_set_displacement(self._h, _ptr(uh)))
+
+    def energy(self):
+        """Energy balance of the last FP64 solve with kinetic_energy=2:
+        kinetic energy, internal work, external (damping) work and the
+        relative balance error, per RVE."""
+        out = {k: np.zeros(self.n_rve) for k in ("kinetic", "internal_work", "external_work",
+                                                 "balance")}
+        _check(_lib.fe2_batch_energy(self._h, _ptr(out["kinetic"]), _ptr(out["internal_work"]),
+                                     _ptr(out["external_work"]), _ptr(out["balance"])))
+        return out
 
     def info(self):
         a, b, c, d = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
