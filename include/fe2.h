@@ -99,7 +99,10 @@ typedef struct {
     double dt_safety;     /* time-step safety factor alpha in (0, 1] (default 0.9) */
     int32_t precision;    /* fe2_precision (default FE2_PREC_MIXED) */
     int32_t init;         /* fe2_init (default FE2_INIT_AFFINE) */
-    int32_t kinetic_energy; /* 1: also track the kinetic energy 1/2 sum m v^2 */
+    int32_t kinetic_energy; /* 1: also track the kinetic energy 1/2 sum m v^2;
+                               2 (FE2_PREC_FP64 only): also the internal and
+                               external work of the energy balance check
+                               (fe2_batch_energy) */
     int32_t block_threads;  /* threads per CTA: 0 = default (512, the paper's
                                team size), else a multiple of 32 in [64, 512] */
     int64_t lead_iters;   /* MIXED: < 0 = lead until the relative residual
@@ -117,7 +120,7 @@ typedef struct {
                              value; when it does not (the FP32 increments have
                              reached their rounding floor), the RVE is handed
                              back to a double-float resume that runs to
-                             convergence. 0 = default 250,000; < 0 = never */
+                             convergence. 0 = default 1,000,000; < 0 = never */
 } fe2_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -301,6 +304,24 @@ fe2_status fe2_batch_results_dev(fe2_batch *b, double *sigma_dev, int64_t *iters
  * double-float lead iterations (MIXED; 0 for FP64). Waits for the solve. */
 fe2_status fe2_batch_diagnostics(fe2_batch *b, double *f_ref, double *kinetic_energy,
                                  int64_t *lead_iters);
+
+/*
+ * Energy balance of the last batched solve (Algorithm 1, "optionally check
+ * energy balance": three reductions over the free DOFs per iteration), per
+ * RVE, HOST memory, any pointer may be NULL. Needs a last solve with
+ * FE2_PREC_FP64 and opts.kinetic_energy = 2 (else FE2_ESTATE). With du the
+ * step's displacement increment dt v^(n-1/2), g the net internal force and
+ * f_d = -c m v^(n-1/2) the damping force, summed over free DOFs:
+ *   kinetic        K = 1/2 sum m |v^n|^2 at the last iteration
+ *   internal_work  Wint = -sum_steps 1/2 du . (g^(n-1) + g^n)  (stored energy)
+ *   external_work  Wext =  sum_steps 1/2 du . (f_d^(n-1) + f_d^n) (damping,
+ *                  <= 0; prescribed nodes do not move during the iteration)
+ *   balance        (K + Wint - Wext) / max(|Wint|, |Wext|, K): the relative
+ *                  balance error, nonzero by the time discretisation
+ * Waits for the solve.
+ */
+fe2_status fe2_batch_energy(fe2_batch *b, double *kinetic, double *internal_work,
+                            double *external_work, double *balance);
 
 /* Cluster size (CTAs) the MIXED solver uses for each RVE (n_rve entries). */
 fe2_status fe2_batch_parts(const fe2_batch *b, int32_t *parts);

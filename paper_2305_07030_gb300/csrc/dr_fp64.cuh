@@ -111,6 +111,15 @@ __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevRes
     }
     __syncthreads();
     // getInternalForces(u); update accelerations (free DOFs).
+    // Energy check (want_ke == 2, Algorithm 1's optional energy balance): per
+    // free DOF the previous internal force gp and damping force fp, and the
+    // trapezoid sums of this step's increment du = dt v^(n-1/2) against them.
+    const bool energy = P.want_ke == 2;
+    double *gp0 = nullptr, *gp1 = nullptr, *gp2 = nullptr, *fp0 = nullptr, *fp1 = nullptr, *fp2 = nullptr;
+    if (energy) {
+        gp0 = S.gp + 3 * n0; gp1 = gp0 + n; gp2 = gp1 + n;
+        fp0 = S.fdp + 3 * n0; fp1 = fp0 + n; fp2 = fp1 + n;
+    }
     acc = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double g0, g1, g2;
@@ -119,6 +128,11 @@ __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevRes
         if (i < nf) {
             const double m = mass[i];
             a0[i] = ddiv(g0, m); a1[i] = ddiv(g1, m); a2[i] = ddiv(g2, m);
+            if (energy) {
+                // the work sums start from the initial force and no damping force
+                gp0[i] = g0; gp1[i] = g1; gp2[i] = g2;
+                fp0[i] = 0.0; fp1[i] = 0.0; fp2[i] = 0.0;
+            }
         }
     }
     const double f0 = dsqrt(block_sum(acc, red));
@@ -130,7 +144,7 @@ __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevRes
     const double mc = -R.c;
     int64_t it = 0;
     int status = RVE_MAXITER;
-    double r = 0.0, ke = 0.0;
+    double r = 0.0, ke = 0.0, wint = 0.0, wext = 0.0;
     for (;;) {
         // partial velocity update; update displacements (free DOFs)
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
@@ -152,7 +166,7 @@ __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevRes
             __syncthreads();
         }
         // getInternalForces; damping force; residual; accelerations; velocity
-        double rs = 0.0, kes = 0.0;
+        double rs = 0.0, kes = 0.0, wis = 0.0, wes = 0.0;
         for (int i = threadIdx.x; i < nf; i += blockDim.x) {
             double g0, g1, g2;
             if (ET) gather_table_fp64(M, R, rowptr, i, S.tf, g0, g1, g2);
@@ -163,6 +177,18 @@ __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevRes
             rs = dadd(rs, dmul(g0, g0));
             rs = dadd(rs, dmul(g1, g1));
             rs = dadd(rs, dmul(g2, g2));
+            if (energy) {
+                const double f0 = dmul(cm, vv0), f1 = dmul(cm, vv1), f2 = dmul(cm, vv2);
+                const double du0 = dmul(dt, vv0), du1 = dmul(dt, vv1), du2 = dmul(dt, vv2);
+                wis = dadd(wis, dmul(du0, dadd(gp0[i], g0)));
+                wis = dadd(wis, dmul(du1, dadd(gp1[i], g1)));
+                wis = dadd(wis, dmul(du2, dadd(gp2[i], g2)));
+                wes = dadd(wes, dmul(du0, dadd(fp0[i], f0)));
+                wes = dadd(wes, dmul(du1, dadd(fp1[i], f1)));
+                wes = dadd(wes, dmul(du2, dadd(fp2[i], f2)));
+                gp0[i] = g0; gp1[i] = g1; gp2[i] = g2;
+                fp0[i] = f0; fp1[i] = f1; fp2[i] = f2;
+            }
             const double aa0 = ddiv(dadd(g0, dmul(cm, vv0)), m);
             const double aa1 = ddiv(dadd(g1, dmul(cm, vv1)), m);
             const double aa2 = ddiv(dadd(g2, dmul(cm, vv2)), m);
@@ -175,6 +201,10 @@ __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevRes
         }
         const double rs_tot = block_sum(rs, red);
         if (P.want_ke) ke = block_sum(kes, red);
+        if (energy) {
+            wint = dsub(wint, dmul(0.5, block_sum(wis, red)));
+            wext = dadd(wext, dmul(0.5, block_sum(wes, red)));
+        }
         r = dsqrt(rs_tot);
         ++it;
         if (!isfinite(r)) { status = RVE_NAN; break; }
@@ -189,6 +219,8 @@ __device__ void solve_rve_fp64(const DevMesh &M, const DevState &S, const DevRes
         O.status[p] = status;
         O.f_ref[p] = f_ref;
         O.ke[p] = ke;
+        if (O.wint) O.wint[p] = wint;
+        if (O.wext) O.wext[p] = wext;
     }
     __syncthreads();
 }

@@ -79,6 +79,8 @@ struct DevState {
     double *tf;                   // FP64: per element, its force on the first node (3)
     float4 *sv;                   // MIXED FP32 kernel without element table: per node
     float2 *sa;                   //   (v, a.x) and (a.y, a.z)
+    double *gp, *fdp;             // FP64 energy check: previous internal and damping
+                                  // force per free DOF [3][N]
 };
 
 struct DevResults {
@@ -89,6 +91,8 @@ struct DevResults {
     double *f_ref;
     double *ke;
     int64_t *lead;    // MIXED: iterations run in the double-float lead
+    double *wint;     // FP64 energy check: stored internal work since the start
+    double *wext;     //   and work of the damping forces
 };
 
 struct SolveParams {
@@ -97,7 +101,8 @@ struct SolveParams {
     int64_t max_iter;
     double alpha;
     int init;
-    int want_ke;
+    int want_ke;          // 1: kinetic energy; 2 (FP64): also the work terms of the
+                          // energy balance
     int64_t lead_iters;   // < 0: lead until the relative residual <= lead_tol
     double lead_tol;
     int rebase_every;

@@ -410,7 +410,7 @@ extern "C" fe2_status fe2_rve_solve_noalloc(int32_t n_nodes, int32_t n_elems, co
     P.max_iter = o.max_iter;
     P.alpha = o.dt_safety;
     P.init = o.init;
-    P.want_ke = o.kinetic_energy;
+    P.want_ke = o.kinetic_energy != 0 ? 1 : 0;  // kinetic energy only: no work-sum scratch here
     P.lead_iters = -1;
     P.lead_tol = 0.0;
     P.smem_positions = 1;

@@ -126,7 +126,7 @@ struct fe2_batch {
     DevBuf<float4> d_dh, d_dl;
     DevBuf<double> d_u, d_v, d_a, d_xg, d_tf;
     DevBuf<float> d_uh, d_ul, d_vh, d_vl, d_ah, d_al, d_fg;
-    DevBuf<double> d_F, d_sigma, d_rel, d_fref, d_ke;
+    DevBuf<double> d_F, d_sigma, d_rel, d_fref, d_ke, d_wint, d_wext, d_gp, d_fdp;
     DevBuf<int64_t> d_iters, d_lead;
     DevBuf<int32_t> d_status, d_queue, d_counters;
     DevBuf<double> d_naive;               // naive comparator scratch (first use)
@@ -135,6 +135,7 @@ struct fe2_batch {
     bool solved = false;
     int32_t last_launches = 0;
     int32_t last_timed = 0;               // persistent launches bracketed by tev
+    int last_energy = 0;                  // kinetic_energy option of the last batched solve
     cudaStream_t last_stream = nullptr;
     std::vector<cudaStream_t> side;       // forked streams for concurrent classes
     std::vector<cudaEvent_t> ev;
@@ -199,6 +200,8 @@ struct fe2_batch {
         s.xg = d_xg.p;
         s.tf = d_tf.p;
         s.sv = d_sv.p;
+        s.gp = d_gp.p;
+        s.fdp = d_fdp.p;
         s.sa = d_sa.p;
         return s;
     }
@@ -206,6 +209,7 @@ struct fe2_batch {
         DevResults r;
         r.sigma = d_sigma.p; r.iters = d_iters.p; r.rel_res = d_rel.p;
         r.status = d_status.p; r.f_ref = d_fref.p; r.ke = d_ke.p; r.lead = d_lead.p;
+        r.wint = d_wint.p; r.wext = d_wext.p;
         return r;
     }
     void release() {
@@ -217,6 +221,7 @@ struct fe2_batch {
         d_uh.release(); d_ul.release(); d_vh.release(); d_vl.release(); d_ah.release();
         d_al.release(); d_fg.release(); d_F.release(); d_sigma.release(); d_rel.release();
         d_fref.release(); d_ke.release(); d_iters.release(); d_lead.release();
+        d_wint.release(); d_wext.release(); d_gp.release(); d_fdp.release();
         d_status.release(); d_queue.release(); d_counters.release(); d_naive.release();
         if (h_F) cudaFreeHost(h_F);
         h_F = nullptr;
@@ -768,6 +773,10 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     A(b->d_rel.alloc(n_rve), "rel");
     A(b->d_fref.alloc(n_rve), "fref");
     A(b->d_ke.alloc(n_rve), "ke");
+    A(b->d_wint.alloc(n_rve), "wint");
+    A(b->d_wext.alloc(n_rve), "wext");
+    A(b->d_gp.alloc(3 * N), "gp");
+    A(b->d_fdp.alloc(3 * N), "fdp");
     A(b->d_iters.alloc(n_rve), "iters");
     A(b->d_lead.alloc(n_rve), "lead");
     A(b->d_status.alloc(n_rve), "status");
@@ -948,6 +957,9 @@ fe2_status check_opts(const fe2_opts &o) {
         return fail(FE2_EINVAL, "block_threads must be 0 or a multiple of 32 in [64, 512]");
     if (!(o.lead_tol >= 0.0) || !std::isfinite(o.lead_tol)) return fail(FE2_EINVAL, "lead_tol must be finite and >= 0");
     if (o.launch != 0 && o.launch != 1) return fail(FE2_EINVAL, "launch must be 0 (graph) or 1 (stream)");
+    if (o.kinetic_energy < 0 || o.kinetic_energy > 2) return fail(FE2_EINVAL, "kinetic_energy must be 0, 1 or 2");
+    if (o.kinetic_energy == 2 && o.precision != FE2_PREC_FP64)
+        return fail(FE2_EINVAL, "the energy-balance work terms (kinetic_energy = 2) need FE2_PREC_FP64");
     return FE2_OK;
 }
 
@@ -1071,7 +1083,7 @@ SolveParams make_params(fe2_batch *b, const fe2_opts &o) {
     P.lead_iters = o.lead_iters;
     P.lead_tol = o.lead_tol;
     P.rebase_every = o.rebase_every;
-    P.stall_window = o.stall_window == 0 ? 250000 : (o.stall_window < 0 ? 0 : o.stall_window);
+    P.stall_window = o.stall_window == 0 ? 1000000 : (o.stall_window < 0 ? 0 : o.stall_window);
     P.resume = 0;
     return P;
 }
@@ -1193,6 +1205,7 @@ fe2_status launch_solve(fe2_batch *b, const fe2_opts &o, cudaStream_t st) {
         timed = b->graph_timed;
     }
     b->last_launches = launches;
+    b->last_energy = o.kinetic_energy;
     b->last_timed = timed / 2;
     b->last_stream = st;
     b->solved = true;
@@ -1266,6 +1279,34 @@ extern "C" fe2_status fe2_batch_diagnostics(fe2_batch *b, double *f_ref, double 
     if (f_ref) CUDA_TRY(cudaMemcpy(f_ref, b->d_fref.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
     if (kinetic_energy) CUDA_TRY(cudaMemcpy(kinetic_energy, b->d_ke.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
     if (lead_iters) CUDA_TRY(cudaMemcpy(lead_iters, b->d_lead.p, sizeof(int64_t) * P, cudaMemcpyDeviceToHost));
+    return FE2_OK;
+}
+
+extern "C" fe2_status fe2_batch_energy(fe2_batch *b, double *kinetic, double *internal_work,
+                                        double *external_work, double *balance) {
+    if (!b) return fail(FE2_EINVAL, "NULL batch");
+    if (!b->solved) return fail(FE2_ESTATE, "no solve has been issued");
+    if (b->last_energy != 2) return fail(FE2_ESTATE, "the last solve did not track the energy balance");
+    CUDA_TRY(cudaStreamSynchronize(b->last_stream));
+    {
+        const fe2_status w = wait_slots(b);
+        if (w != FE2_OK) return w;
+    }
+    const size_t P = b->n_rve;
+    std::vector<double> k(P), wi(P), we(P);
+    CUDA_TRY(cudaMemcpy(k.data(), b->d_ke.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(wi.data(), b->d_wint.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(we.data(), b->d_wext.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    for (size_t p = 0; p < P; ++p) {
+        if (kinetic) kinetic[p] = k[p];
+        if (internal_work) internal_work[p] = wi[p];
+        if (external_work) external_work[p] = we[p];
+        if (balance) {
+            const double scale = std::max(std::max(std::fabs(wi[p]), std::fabs(we[p])), k[p]);
+            const double err = k[p] + wi[p] - we[p];
+            balance[p] = scale > 0.0 ? err / scale : 0.0;
+        }
+    }
     return FE2_OK;
 }
 
@@ -1398,6 +1439,7 @@ extern "C" fe2_status fe2_batch_solve_naive(fe2_batch *b, const double *F, const
     CUDA_TRY(cudaMemcpyAsync(b->d_status.p, stat.data(), sizeof(int32_t) * b->n_rve, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     b->last_launches = launches;
+    b->last_energy = 0;
     b->last_timed = 0;
     b->last_stream = st;
     b->solved = true;
@@ -1455,6 +1497,7 @@ extern "C" fe2_status fe2_batch_submit(fe2_batch *b, int32_t n, const int32_t *r
     for (size_t k = 0; k < b->slots.size(); ++k)
         if (!b->slots[k].busy) { slot = (int)k; break; }
     if (slot < 0) return fail(FE2_EBUSY, "every serving slot is in flight");
+    b->last_energy = 0;  // the submission rewrites part of the per-RVE results
     ServeSlot &sl = b->slots[slot];
     const bool fp64 = o.precision == FE2_PREC_FP64;
     auto &classes = fp64 ? b->classes_fp64 : b->classes_mixed;

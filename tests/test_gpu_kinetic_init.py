@@ -130,3 +130,30 @@ def test_mixed_warm_start_against_oracle():
         e = rel_err(second["sigma"][p], r["sigma"])
         print(f"warm start RVE {p}: err {e:.2e} family diameter {spread:.2e}")
         assert e <= mixed_bound(spread), (p, e, spread)
+
+
+@pytest.mark.parametrize("max_iter", [60, 10_000_000])
+def test_energy_balance_fp64(max_iter):
+    """Algorithm 1's optional energy check, all three terms (kinetic energy,
+    internal work, damping work) against the oracle: FP64 mode runs the
+    oracle's trajectory, so only the sums are reassociated (1e-11)."""
+    from paper_2305_07030_gb300 import FE2Error
+    w = _workload([37, 300, 777], seed=45)
+    ref = oracle.solve_batch(w, init=1, max_iter=max_iter, want_energy=True)
+    with Batch(w.nets, damping=w.damping) as b:
+        b.solve(w.F, precision="fp64", kinetic_energy="balance", max_iter=max_iter)
+        out = b.stress()
+        e = b.energy()
+        for p, r in enumerate(ref):
+            assert out["iters"][p] == r["iters"]
+            assert abs(e["kinetic"][p] - r["ke"]) <= 1e-11 * r["ke"] + 1e-300
+            assert abs(e["internal_work"][p] - r["wint"]) <= 1e-11 * abs(r["wint"])
+            assert abs(e["external_work"][p] - r["wext"]) <= 1e-11 * abs(r["wext"])
+            bal = (r["ke"] + r["wint"] - r["wext"]) / max(abs(r["wint"]), abs(r["wext"]), r["ke"])
+            assert abs(e["balance"][p] - bal) <= 1e-9
+        # the work terms are FP64-only; a mixed solve leaves nothing to report
+        with pytest.raises(FE2Error):
+            b.solve(w.F, precision="mixed", kinetic_energy="balance")
+        b.solve(w.F, precision="fp64", kinetic_energy=True, max_iter=5)
+        with pytest.raises(FE2Error):
+            b.energy()

@@ -254,3 +254,32 @@ def test_invalid_inputs_rejected():
     with Batch([net]) as b:
         with pytest.raises(FE2Error):
             b.solve(np.eye(3)[None], max_iter=0)
+
+
+def test_stall_hand_back_resumes_in_double_float():
+    """An RVE whose FP32 residual stops falling goes back to the double-float
+    kernel, which runs it to convergence. With a stall window of one FP32
+    evaluation every RVE is handed back at once: all still converge to an
+    oracle-verified equilibrium within the mixed bound, and nearly all of
+    their iterations run in double-float; with the default window none is
+    handed back on these well-behaved RVEs."""
+    w = _workload([200, 512, 900], seed=14)
+    env = envelope_batch(w)
+    with Batch(w.nets, damping=w.damping) as b:
+        b.solve(w.F, precision="mixed", stall_window=1)
+        out = b.stress()
+        lead = b.diagnostics()["lead_iters"]
+        u = b.displacement()
+        off = b.node_off
+        b.solve(w.F, precision="mixed")
+        plain = b.stress()
+        lead_plain = b.diagnostics()["lead_iters"]
+    for p, (r, diam) in enumerate(env):
+        assert out["status"][p] == "OK" and plain["status"][p] == "OK"
+        res, s_at_u = check_equilibrium(w.nets[p], w.F[p], u[off[p]:off[p + 1]], r["f_ref"], 1e-8)
+        assert res <= 1.5e-8, (p, res)
+        assert rel_err(out["sigma"][p], s_at_u) <= 1e-12
+        assert rel_err(out["sigma"][p], r["sigma"]) <= mixed_bound(diam)
+        # handed back after a few FP32 evaluations: the rest ran in double-float
+        assert out["iters"][p] - lead[p] <= 8, (p, out["iters"][p], lead[p])
+        assert plain["iters"][p] - lead_plain[p] > 8
