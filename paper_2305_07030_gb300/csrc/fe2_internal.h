@@ -41,6 +41,9 @@ struct RveDesc {
     int32_t part_free_max;  // most free nodes in one part
     int32_t part_elem_max;  // FP32 kernel: most table elements of one part
     int32_t part_slot_max;  // FP32 kernel: most row slots (ELL, 32-node slabs) of one part
+    int64_t slot0;          // FP64 cluster kernel: first element slot of this RVE
+    int32_t part_fslot_max; // FP64 cluster kernel: most element slots of one part
+    int32_t pad_;
 };
 
 // Read-only, create-time arrays.
@@ -64,6 +67,11 @@ struct DevMesh {
     const int32_t *csr_el;        // per CSR entry: RVE-local element << 1, | 1 when
                                   // the row's node is the element's second node
                                   // (caller orientation)
+    const int4 *fp_slot;          // FP64 cluster kernel, per element slot: (element,
+                                  // first end, second end, 0), ends as (part << 16 | index)
+    const int32_t *fp_csr_slot;   // per CSR entry of a free node: part-relative slot << 1
+                                  // | 1 when the node is the element's second end
+    const int32_t *fp_part_slot;  // per RVE kMaxParts+1 part slot offsets (from slot0)
 };
 
 // Mutable solver state (device).
@@ -81,6 +89,10 @@ struct DevState {
     float2 *sa;                   //   (v, a.x) and (a.y, a.z)
     double *gp, *fdp;             // FP64 energy check: previous internal and damping
                                   // force per free DOF [3][N]
+    double *ualt;                 // FP64 cluster kernel: displacement of odd evaluations,
+                                  // per RVE [3][n] at 3 node0
+    double *fpt;                  // FP64 cluster kernel: element forces [3][part slots]
+                                  // when the table does not fit in shared memory
 };
 
 struct DevResults {
@@ -147,6 +159,13 @@ size_t mixed_fp32_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, s
 size_t mixed_lead_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, size_t limit);
 // Whether a launch with `smem` bytes uses the shared-memory element table.
 bool mixed_staged(int lead, size_t smem, int part_cap);
+// FP64 cluster kernel (dr_fp64_cluster.cu): dynamic shared memory (two
+// position buffers, and the element table when tsm), launch, occupancy.
+size_t fp64_cluster_smem(int part_cap, int slot_cap, bool tsm);
+int launch_dr_fp64_cluster(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
+                           int clusters, int parts, int block, int part_cap, int slot_cap, bool tsm,
+                           void *stream);
+int occupancy_dr_fp64_cluster(int parts, int block, int part_cap, int slot_cap, bool tsm);
 // Shared memory per node of a kernel without its element table.
 size_t mixed_plain_node_bytes(int lead);
 // Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.

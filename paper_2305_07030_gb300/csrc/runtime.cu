@@ -67,6 +67,9 @@ struct SizeClass {
     int block_lead = 0;         // mixed: tuned CTA sizes (0 = default)
     int block_fp32 = 0;
     int smem_positions = 1;     // FP64: positions in shared memory
+    bool fp64_cluster = false;  // FP64: one cluster of `parts` CTAs per RVE
+    bool fp64_tsm = false;      // FP64 cluster: element table in shared memory
+    int fslot_max = 0;          // FP64 cluster: most element slots of one part
     size_t smem_bytes = 0;      // dynamic shared memory per CTA
     int part_max = 0;           // mixed: largest part (nodes)
     int free_max = 0;           // mixed: most free nodes in one part
@@ -121,6 +124,9 @@ struct fe2_batch {
     DevBuf<double> d_X, d_mass, d_EA_csr, d_L_csr, d_el_EA, d_el_L;
     DevBuf<float> d_Xh, d_Xl, d_imh, d_iml;
     DevBuf<int32_t> d_rowptr, d_col, d_col_part, d_part_off, d_el_a, d_el_b, d_csr_el;
+    DevBuf<int32_t> d_fp_csr_slot, d_fp_part_slot;
+    DevBuf<int4> d_fp_slot;
+    DevBuf<double> d_ualt, d_fpt;
     DevBuf<float2> d_eaf, d_eaf_lo, d_sa;
     DevBuf<float4> d_sv;
     DevBuf<float4> d_dh, d_dl;
@@ -188,6 +194,9 @@ struct fe2_batch {
         m.el_EA = d_el_EA.p;
         m.el_L = d_el_L.p;
         m.csr_el = d_csr_el.p;
+        m.fp_slot = d_fp_slot.p;
+        m.fp_csr_slot = d_fp_csr_slot.p;
+        m.fp_part_slot = d_fp_part_slot.p;
         return m;
     }
     DevState state() const {
@@ -201,6 +210,8 @@ struct fe2_batch {
         s.tf = d_tf.p;
         s.sv = d_sv.p;
         s.gp = d_gp.p;
+        s.ualt = d_ualt.p;
+        s.fpt = d_fpt.p;
         s.fdp = d_fdp.p;
         s.sa = d_sa.p;
         return s;
@@ -216,7 +227,7 @@ struct fe2_batch {
         d_rve.release(); d_X.release(); d_mass.release(); d_EA_csr.release(); d_L_csr.release();
         d_el_EA.release(); d_el_L.release(); d_Xh.release(); d_Xl.release(); d_imh.release();
         d_iml.release(); d_rowptr.release(); d_col.release(); d_col_part.release();
-        d_part_off.release(); d_el_a.release(); d_el_b.release(); d_csr_el.release(); d_tf.release(); d_sv.release(); d_sa.release(); d_eaf.release();
+        d_part_off.release(); d_el_a.release(); d_el_b.release(); d_csr_el.release(); d_fp_csr_slot.release(); d_fp_part_slot.release(); d_fp_slot.release(); d_ualt.release(); d_fpt.release(); d_tf.release(); d_sv.release(); d_sa.release(); d_eaf.release();
         d_eaf_lo.release(); d_dh.release(); d_dl.release(); d_u.release(); d_v.release(); d_a.release(); d_xg.release();
         d_uh.release(); d_ul.release(); d_vh.release(); d_vl.release(); d_ah.release();
         d_al.release(); d_fg.release(); d_F.release(); d_sigma.release(); d_rel.release();
@@ -353,10 +364,46 @@ void build_classes(const std::vector<RveDesc> &rve, const std::vector<int32_t> &
     });
     const size_t cap = smem_optin - 16384;  // room for static shared memory
     if (precision == FE2_PREC_FP64) {
+        // RVEs of several parts run on a cluster (one part per CTA) when its
+        // position buffers fit; classes by (parts, table in shared memory).
+        // FE2_FP64_CLUSTER=0 keeps every RVE on the single-CTA kernel.
+        const bool clusters = env_int("FE2_FP64_CLUSTER", 1) != 0;
+        auto on_cluster = [&](const RveDesc &R) {
+            return clusters && R.n_parts >= 2 && fp64_cluster_smem(R.part_max, 0, false) <= cap;
+        };
+        for (int32_t p : order) {
+            const RveDesc &R = rve[p];
+            if (!on_cluster(R)) continue;
+            const bool tsm = fp64_cluster_smem(R.part_max, R.part_fslot_max, true) <= cap;
+            SizeClass *c = nullptr;
+            for (auto &k : out)
+                if (k.parts == R.n_parts && k.fp64_tsm == tsm &&
+                    (!tsm || fp64_cluster_smem(std::max(k.part_max, R.part_max),
+                                               std::max(k.fslot_max, R.part_fslot_max), true) <= cap)) {
+                    c = &k;
+                    break;
+                }
+            if (!c) {
+                out.emplace_back();
+                c = &out.back();
+                c->parts = R.n_parts;
+                c->fp64_cluster = true;
+                c->fp64_tsm = tsm;
+                c->smem_positions = 0;
+            }
+            c->rves.push_back(p);
+            c->part_max = std::max(c->part_max, R.part_max);
+            c->fslot_max = std::max(c->fslot_max, R.part_fslot_max);
+            c->smem_bytes = fp64_cluster_smem(c->part_max, c->fslot_max, c->fp64_tsm);
+        }
+        std::stable_sort(out.begin(), out.end(), [](const SizeClass &a, const SizeClass &b) {
+            return a.parts > b.parts;
+        });
         const size_t bounds[] = {16u << 10, 32u << 10, 56u << 10, 112u << 10, cap};
         std::vector<SizeClass> cls(6);
         cls[5].smem_positions = 0;
         for (int32_t p : order) {
+            if (on_cluster(rve[p])) continue;
             const size_t need = (size_t)24 * rve[p].n_nodes;
             int c = 5;
             for (int k = 0; k < 5; ++k)
@@ -506,6 +553,12 @@ struct HostLayout {
     std::vector<double> X, EAcsr, ElEA;  // X as SoA [3][N]
     std::vector<int32_t> col, colp, Ela, Elb, row, part, csrEl;
     std::vector<int64_t> ElemOf, Ga, Gb;
+    // FP64 cluster kernel: per part, one slot per element with an end among
+    // the part's free nodes (first use in row order); per slot (element,
+    // first end, second end) with ends as (part << 16 | index in part); per
+    // CSR entry of a free node its slot << 1 | 1 when the node is the second
+    // end; per RVE the parts' slot offsets (relative to RveDesc::slot0)
+    std::vector<int32_t> fpSlot, fpCsrSlot, fpPartSlot;
 };
 
 void build_layout(int32_t n_rve, const int64_t *node_off, const double *X, const int64_t *elem_off,
@@ -521,6 +574,9 @@ void build_layout(int32_t n_rve, const int64_t *node_off, const double *X, const
     L.col.assign(2 * E, 0);
     L.colp.assign(2 * E, 0);
     L.csrEl.assign(2 * E, 0);
+    L.fpCsrSlot.assign(2 * E, -1);
+    L.fpPartSlot.assign((size_t)n_rve * (kMaxParts + 1), 0);
+    L.fpSlot.clear();
     L.Ela.assign(E, 0);
     L.Elb.assign(E, 0);
     L.ElemOf.assign(2 * E, 0);
@@ -663,6 +719,35 @@ void build_layout(int32_t n_rve, const int64_t *node_off, const double *X, const
             }
         }
         hrow[R.rp0 + n] = pos;
+        // FP64 cluster slot tables (see HostLayout)
+        {
+            R.slot0 = (int64_t)(L.fpSlot.size() / 4);
+            int32_t *ps = L.fpPartSlot.data() + (size_t)p * (kMaxParts + 1);
+            std::vector<int32_t> slot_of(ne, -1);
+            int32_t ns = 0, fslot_max = 0;
+            for (int r = 0; r < C; ++r) {
+                ps[r] = ns;
+                const int32_t first = ns;
+                for (int k = pf[r]; k < pf[r + 1]; ++k) {
+                    for (int32_t q = hrow[R.rp0 + k]; q < hrow[R.rp0 + k + 1]; ++q) {
+                        const int32_t w = L.csrEl[csr_pos + q];
+                        const int32_t e = w >> 1;
+                        if (slot_of[e] < first) {  // not yet a slot of this part
+                            slot_of[e] = ns++;
+                            const int a = conn[2 * (e0 + e)], c2 = conn[2 * (e0 + e) + 1];
+                            L.fpSlot.push_back(e);
+                            L.fpSlot.push_back((owner[a] << 16) | local[a]);
+                            L.fpSlot.push_back((owner[c2] << 16) | local[c2]);
+                            L.fpSlot.push_back(0);
+                        }
+                        L.fpCsrSlot[csr_pos + q] = ((slot_of[e] - first) << 1) | (w & 1);
+                    }
+                }
+                fslot_max = std::max(fslot_max, ns - first);
+            }
+            for (int r = C; r <= kMaxParts; ++r) ps[r] = ns;
+            R.part_fslot_max = fslot_max;
+        }
         csr_pos += pos;
         for (int64_t e = e0; e < e0 + ne; ++e) {
             // the caller's orientation (a, b) is kept for lengths and the stress sum
@@ -748,6 +833,12 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     A(b->d_col.alloc(2 * E), "col");
     A(b->d_col_part.alloc(2 * E), "col_part");
     A(b->d_csr_el.alloc(2 * E), "csr_el");
+    const size_t n_fslots = L.fpSlot.size() / 4;
+    A(b->d_fp_slot.alloc(std::max<size_t>(1, n_fslots)), "fp_slot");
+    A(b->d_fp_csr_slot.alloc(2 * E), "fp_csr_slot");
+    A(b->d_fp_part_slot.alloc(L.fpPartSlot.size()), "fp_part_slot");
+    A(b->d_ualt.alloc(3 * N), "ualt");
+    A(b->d_fpt.alloc(3 * std::max<size_t>(1, n_fslots)), "fpt");
     A(b->d_tf.alloc(3 * E), "tf");
     A(b->d_sv.alloc(N), "sv");
     A(b->d_sa.alloc(N), "sa");
@@ -794,6 +885,9 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
     H2D(b->d_col.p, hcol.data(), sizeof(int32_t) * 2 * E, "col");
     H2D(b->d_col_part.p, hcolp.data(), sizeof(int32_t) * 2 * E, "col_part");
     H2D(b->d_csr_el.p, L.csrEl.data(), sizeof(int32_t) * 2 * E, "csr_el");
+    if (n_fslots) H2D(b->d_fp_slot.p, L.fpSlot.data(), sizeof(int4) * n_fslots, "fp_slot");
+    H2D(b->d_fp_csr_slot.p, L.fpCsrSlot.data(), sizeof(int32_t) * 2 * E, "fp_csr_slot");
+    H2D(b->d_fp_part_slot.p, L.fpPartSlot.data(), sizeof(int32_t) * L.fpPartSlot.size(), "fp_part_slot");
     H2D(b->d_rowptr.p, hrow.data(), sizeof(int32_t) * (N + n_rve), "rowptr");
     H2D(b->d_part_off.p, hpart.data(), sizeof(int32_t) * hpart.size(), "part_off");
     H2D(b->d_el_a.p, hEla.data(), sizeof(int32_t) * E, "el_a");
@@ -1004,8 +1098,17 @@ int resident_of(fe2_batch *b, int kind, int parts, int block, size_t smem, int p
     const auto key = std::make_tuple(kind, parts, block, smem, part_cap);
     auto it = b->occ.find(key);
     if (it != b->occ.end()) return it->second;
-    const int r = kind == 2 ? occupancy_dr_fp64(parts, block, smem)
-                            : occupancy_dr_mixed(kind, parts, block, smem, part_cap);
+    // kind: 0/1 mixed FP32/lead, 2 FP64 single CTA (parts = positions staged),
+    // 3 FP64 cluster (smem encodes the table choice through its size)
+    int r;
+    if (kind == 3) {
+        const size_t plain = fp64_cluster_smem(part_cap, 0, false);
+        const int slots = smem > plain ? (int)((smem - plain) / (3 * sizeof(double))) : 0;
+        r = occupancy_dr_fp64_cluster(parts, block, part_cap, slots, smem > plain);
+    } else {
+        r = kind == 2 ? occupancy_dr_fp64(parts, block, smem)
+                      : occupancy_dr_mixed(kind, parts, block, smem, part_cap);
+    }
     b->occ[key] = r;
     return r;
 }
@@ -1026,7 +1129,24 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
     P.queue_len = nq;
     P.counter = counters;
     P.smem_positions = c.smem_positions;
-    if (fp64) {
+    if (fp64 && c.fp64_cluster) {
+        const int block = o.block_threads ? o.block_threads : 512;
+        const int resident = resident_of(b, 3, c.parts, block, c.smem_bytes, c.part_max);
+        if (resident < 1)
+            return fail(FE2_ECUDA, "no FP64 cluster of " + std::to_string(c.parts) + " CTAs fits");
+        if (timed) {
+            if (*timed + 2 > (int)b->tev.size()) return fail(FE2_ECUDA, "too many launch classes");
+            CUDA_TRY(record_timing(b->tev[*timed], s, capturing));
+        }
+        const int e = launch_dr_fp64_cluster(M, S, R, P, std::min(nq, resident), c.parts, block, c.part_max,
+                                             c.fslot_max, c.fp64_tsm, s);
+        if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
+        if (timed) {
+            CUDA_TRY(record_timing(b->tev[*timed + 1], s, capturing));
+            *timed += 2;
+        }
+        ++*launches;
+    } else if (fp64) {
         const int block = o.block_threads ? o.block_threads : 512;
         const size_t smem = c.smem_positions ? c.smem_bytes : 0;
         const int per_sm = std::max(1, resident_of(b, 2, c.smem_positions, block, smem, 0));
@@ -1133,6 +1253,12 @@ fe2_status warm_shapes(fe2_batch *b, const fe2_opts &o) {
     const bool fp64 = o.precision == FE2_PREC_FP64;
     const size_t limit = b->smem_optin - 16384;
     for (const SizeClass &c : fp64 ? b->classes_fp64 : b->classes_mixed) {
+        if (fp64 && c.fp64_cluster) {
+            const int block = o.block_threads ? o.block_threads : 512;
+            if (resident_of(b, 3, c.parts, block, c.smem_bytes, c.part_max) < 1)
+                return fail(FE2_ECUDA, "no FP64 cluster of " + std::to_string(c.parts) + " CTAs fits");
+            continue;
+        }
         if (fp64) {
             const int block = o.block_threads ? o.block_threads : 512;
             resident_of(b, 2, c.smem_positions, block, c.smem_positions ? c.smem_bytes : 0, 0);

@@ -138,7 +138,7 @@ def test_energy_balance_fp64(max_iter):
     internal work, damping work) against the oracle: FP64 mode runs the
     oracle's trajectory, so only the sums are reassociated (1e-11)."""
     from paper_2305_07030_gb300 import FE2Error
-    w = _workload([37, 300, 777], seed=45)
+    w = _workload([37, 300, 777, 1500], seed=45)  # 1500 nodes: the cluster kernel
     ref = oracle.solve_batch(w, init=1, max_iter=max_iter, want_energy=True)
     with Batch(w.nets, damping=w.damping) as b:
         b.solve(w.F, precision="fp64", kinetic_energy="balance", max_iter=max_iter)

@@ -56,9 +56,11 @@ def test_fp64_bitwise_trajectory(init):
         assert abs(out["rel_res"][p] - r["rel_res"]) <= 1e-12 * max(r["rel_res"], 1e-300) + 1e-300
 
 
-def test_fp64_global_scratch_class_and_maxiter():
-    """An RVE too big to stage in shared memory runs from L2 scratch; the
-    trajectory is still the oracle's (checked after a fixed iteration cap)."""
+def test_fp64_global_scratch_class_and_maxiter(monkeypatch):
+    """An RVE too big to stage in shared memory on one CTA runs from L2
+    scratch when the cluster kernel is switched off; the trajectory is still
+    the oracle's (checked after a fixed iteration cap)."""
+    monkeypatch.setenv("FE2_FP64_CLUSTER", "0")
     w = _workload([10500], seed=12)
     ref = oracle.solve_batch(w, init=1, max_iter=400)
     out = _solve(w, precision="fp64", max_iter=400)
@@ -66,6 +68,29 @@ def test_fp64_global_scratch_class_and_maxiter():
     assert out["iters"][0] == 400
     assert np.array_equal(out["u"], ref[0]["u"])
     assert rel_err(out["sigma"][0], ref[0]["sigma"]) <= 1e-12
+
+
+@pytest.mark.parametrize("max_iter", [400, 300000])
+def test_fp64_cluster_kernel_bitwise_trajectory(max_iter):
+    """RVEs of several parts run the FP64 cluster kernel (one part per CTA,
+    neighbours through distributed shared memory, element slots per part):
+    the trajectory is still the oracle's bit for bit, at a fixed iteration
+    cap (2, 4, 8 and 16 parts, the largest with its element table in global
+    memory) and to convergence."""
+    sizes = [1500, 3000, 6000, 40000] if max_iter == 400 else [1300, 2600]
+    w = _workload(sizes, seed=15)
+    from paper_2305_07030_gb300 import plan
+    assert sorted(set(int(x) for x in plan(w.nets)["parts"])) == \
+        ([2, 4, 8, 16] if max_iter == 400 else [2, 4])
+    ref = oracle.solve_batch(w, init=1, tol=1e-8, max_iter=max_iter)
+    out = _solve(w, precision="fp64", init="affine", tol=1e-8, max_iter=max_iter)
+    for p, r in enumerate(ref):
+        a, b = out["node_off"][p], out["node_off"][p + 1]
+        assert out["status"][p] == r["status"]
+        assert out["iters"][p] == r["iters"], (p, out["iters"][p], r["iters"])
+        assert np.array_equal(out["u"][a:b], r["u"]), np.abs(out["u"][a:b] - r["u"]).max()
+        assert rel_err(out["sigma"][p], r["sigma"]) <= 1e-12
+        assert abs(out["rel_res"][p] - r["rel_res"]) <= 1e-12 * max(r["rel_res"], 1e-300) + 1e-300
 
 
 def test_mixed_within_tolerance_or_rounding_envelope():
