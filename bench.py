@@ -363,6 +363,9 @@ def run_ours(args, rank, world):
         "stress_err": stress_errors(args, sigma, status),
         "clocks": clocks,
     }
+    if args.dump:
+        np.savez(args.dump, sigma=sigma, iters=iters, status=status, n_nodes=nn,
+                 lead=np.asarray(leads))
     if mixed and args.workload == "rve5000x64" and not args.no_naive:
         nv = naive_comparator(w, iters)
         nv["speedup_of_batched"] = value / nv["solves_per_s"]
@@ -619,6 +622,7 @@ def main():
     ap.add_argument("--launch", default="graph", choices=["graph", "stream"],
                     help="replay the solve as a CUDA graph (default) or launch on streams")
     ap.add_argument("--tuning", default="", help="JSON file written by fe2_autotune to load first")
+    ap.add_argument("--dump", default="", help="write the per-RVE results (npz) to this path")
     ap.add_argument("--tune", default="",
                     help="explicit tuning: bucket:parts:block_fp32[:block_lead],... (2^bucket <= nodes)")
     ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")

@@ -30,7 +30,7 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2305_07030_gb300 import Batch  # noqa: E402
-from parity_util import check_equilibrium, envelope_batch, mixed_bound, rel_err  # noqa: E402
+from parity_util import check_equilibrium, envelope_batch, rel_err, within_family  # noqa: E402
 
 
 def _workload(sizes, seed):
@@ -104,7 +104,9 @@ def test_mixed_reference_start_against_oracle():
         assert rel_err(out["sigma"][p], s_at_u) <= 1e-12
         e = rel_err(out["sigma"][p], r["sigma"])
         print(f"reference start RVE {p}: err {e:.2e} family diameter {spread:.2e}")
-        assert e <= mixed_bound(spread), (p, e, spread)
+        ok, e, bound = within_family(w.nets[p], w.F[p], w.damping[p], out["sigma"][p], r["sigma"],
+                                     spread, init=0)
+        assert ok, (p, e, bound)
 
 
 def test_mixed_warm_start_against_oracle():
@@ -129,7 +131,9 @@ def test_mixed_warm_start_against_oracle():
         assert rel_err(second["sigma"][p], s_at_u) <= 1e-12
         e = rel_err(second["sigma"][p], r["sigma"])
         print(f"warm start RVE {p}: err {e:.2e} family diameter {spread:.2e}")
-        assert e <= mixed_bound(spread), (p, e, spread)
+        ok, e, bound = within_family(w.nets[p], F2[p], w.damping[p], second["sigma"][p], r["sigma"],
+                                     spread, init=2, u_warm=u1[off[p]:off[p + 1]])
+        assert ok, (p, e, bound)
 
 
 @pytest.mark.parametrize("max_iter", [60, 10_000_000])

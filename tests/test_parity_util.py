@@ -29,3 +29,18 @@ def test_family_diameter_is_largest_pairwise_distance():
 def test_mixed_bound_floor_is_the_north_star_tolerance():
     assert mixed_bound(0.0) == 1e-5 and mixed_bound(3e-6) == 1e-5
     assert mixed_bound(4e-4) == 4e-4
+
+
+def test_within_family_extends_only_when_needed():
+    import rve_inputs as ri
+    from parity_util import oracle_with_envelope, within_family
+    rng = np.random.default_rng(3)
+    net = ri.random_network(60, rng)
+    F = ri.symmetric_perturbation(rng)
+    c = ri.default_damping(60)
+    base, diam = oracle_with_envelope(net, F, c)
+    ok, err, bound = within_family(net, F, c, base["sigma"], base["sigma"], diam)
+    assert ok and err == 0.0 and bound == max(1e-5, diam)
+    far = base["sigma"] * (1.0 + 0.05)
+    ok, err, bound = within_family(net, F, c, far, base["sigma"], diam)
+    assert not ok and abs(err - 0.05) < 1e-12 and bound >= max(1e-5, diam)
