@@ -219,7 +219,8 @@ def run_ours(args, rank, world):
     mixed = args.precision == "mixed"
     batch = fe2.Batch(nets, damping=w.damping)
     opts = dict(precision=args.precision, init="affine", tol=1e-8, max_iter=args.max_iter,
-                lead_iters=args.lead_iters, block_threads=args.block, launch=args.launch)
+                lead_iters=args.lead_iters, lead_tol=args.lead_tol, block_threads=args.block,
+                launch=args.launch)
     F_host = np.ascontiguousarray(w.F.reshape(P, 9))
     F_dev = torch.tensor(F_host.reshape(-1), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -347,12 +348,14 @@ def run_ours(args, rank, world):
         "vs_baseline": None,
         "dtype": "f32+f64" if mixed else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload][1], "precision": args.precision,
-                   "rves": P, "nodes": int(nn.sum()),
-                   "launch": args.launch, "l2": "flushed between steps (256 MB write)",
-                   "tuning": {str(k): list(v) for k, v in fe2.tuning_get().items()},
-                   "classes": _plan_summary(fe2, nets) if mixed else None,
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        # the workload alone, identical in the reference arm's line
+        "config": {"workload": WORKLOADS[args.workload][1]},
+        "run": {"precision": args.precision, "rves": P, "nodes": int(nn.sum()),
+                "launch": args.launch, "lead_tol": args.lead_tol,
+                "l2": "flushed between steps (256 MB write)",
+                "tuning": {str(k): list(v) for k, v in fe2.tuning_get().items()},
+                "classes": _plan_summary(fe2, nets) if mixed else None,
+                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "dof_iters_per_s": world * dof_iters / mean_step,
         "iters": {"mean": float(iters.mean()), "min": int(iters.min()), "max": int(iters.max())},
         "converged": int((status == 0).sum()),
@@ -466,7 +469,8 @@ def run_reference(args):
             "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload][1], "precision": "fp64 (oracle)"},
+            "config": {"workload": WORKLOADS[args.workload][1]},
+            "run": {"precision": "fp64 (oracle)", "parallelism": f"{k} host threads"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": k, "kind": "oracle",
                              "sample": f"{k} RVEs on {k} threads, at most {cap} iterations each "
                                        f"per step; solves/s = DOF-iters/s / {per_solve:.4g} "
@@ -618,6 +622,8 @@ def main():
     ap.add_argument("--rves", default="", help="comma-separated RVE subset (profiling runs)")
     ap.add_argument("--max-iter", type=int, default=10_000_000)
     ap.add_argument("--lead-iters", type=int, default=-1)
+    ap.add_argument("--lead-tol", type=float, default=1e-3,
+                    help="mixed: relative residual that ends the double-float lead")
     ap.add_argument("--block", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--launch", default="graph", choices=["graph", "stream"],
                     help="replay the solve as a CUDA graph (default) or launch on streams")
