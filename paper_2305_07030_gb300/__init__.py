@@ -286,7 +286,7 @@ def plan(nets, smem_optin=232448, nodes_per_cta=0):
     CTA, whether the element table is staged in it, and the CTA size."""
     n_rve = len(nets)
     node_off, X, elem_off, conn, EA, fixed = _pack_inputs(nets)
-    m = 8
+    m = max(8, n_rve)  # classes never outnumber RVEs
     ncls = C.c_int32()
     out = {"rve_class": np.zeros(n_rve, np.int32), "parts": np.zeros(m, np.int32),
            "rves": np.zeros(m, np.int32), "smem": np.zeros(2 * m, np.int64),

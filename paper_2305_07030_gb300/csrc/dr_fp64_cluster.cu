@@ -97,13 +97,17 @@ __device__ __forceinline__ void cl_wait() {
 
 }  // namespace
 
-// One RVE on the cluster. X (smem) is this CTA's [2][3][part_cap] position
+// One RVE on the cluster. XB (smem) is this CTA's [2][3][part_cap] position
 // buffers; T the element table, [3][slot_cap] in shared memory (TSM) or this
-// part's region of the global table.
-template <bool TSM>
+// part's region of the global table. With SSM the own free nodes' state lives
+// in shared memory too (ST: displacement [2][3][free_cap], velocity and
+// acceleration [3][free_cap] each, mass [free_cap]); otherwise in global
+// memory (L2).
+template <bool TSM, bool SSM>
 __device__ void solve_rve_fp64_cluster(cg::cluster_group &cl, Fp64ClusterShared &sh, const DevMesh &M,
                                        const DevState &S, const DevResults &O, const SolveParams &P, int p,
-                                       double *XB, double *Tsm, int part_cap, int slot_cap) {
+                                       double *XB, double *ST, double *Tsm, int part_cap, int free_cap,
+                                       int slot_cap) {
     const RveDesc R = M.rve[p];
     const int me = (int)cl.block_rank(), C = (int)cl.num_blocks();
     const int32_t *po = M.part_off + (int64_t)p * 2 * (kMaxParts + 1);
@@ -127,9 +131,23 @@ __device__ void solve_rve_fp64_cluster(cg::cluster_group &cl, Fp64ClusterShared 
     // in the alternate [3][n] block (selected per iteration, no indexed arrays)
     double *const ue0 = S.u0 + n0, *const ue1 = S.u1 + n0, *const ue2 = S.u2 + n0;
     double *const uo0 = S.ualt + 3 * n0, *const uo1 = uo0 + n, *const uo2 = uo1 + n;
+    // free-node state, addressed by the RVE-local node id i = f0 + k: shared
+    // arrays are offset by -f0 so that the same index serves both places
     double *v0 = S.v0 + n0, *v1 = S.v1 + n0, *v2 = S.v2 + n0;
     double *a0 = S.a0 + n0, *a1 = S.a1 + n0, *a2 = S.a2 + n0;
     const double *mass = M.mass + n0;
+    double *su[2][3] = {};
+    if (SSM) {
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 3; ++c) su[b][c] = ST + (3 * b + c) * free_cap - f0;
+        double *sv = ST + 6 * free_cap - f0;
+        v0 = sv; v1 = sv + free_cap; v2 = sv + 2 * free_cap;
+        double *sa = ST + 9 * free_cap - f0;
+        a0 = sa; a1 = sa + free_cap; a2 = sa + 2 * free_cap;
+        double *sm = ST + 12 * free_cap - f0;
+        for (int k = threadIdx.x; k < nfr; k += blockDim.x) sm[f0 + k] = M.mass[n0 + f0 + k];
+        mass = sm;
+    }
     double *const x0b = XB, *const x1b = XB + 3 * part_cap;
     const bool energy = P.want_ke == 2;
     double *gp0 = nullptr, *gp1 = nullptr, *gp2 = nullptr, *fp0 = nullptr, *fp1 = nullptr, *fp2 = nullptr;
@@ -173,7 +191,12 @@ __device__ void solve_rve_fp64_cluster(cg::cluster_group &cl, Fp64ClusterShared 
             else u[r] = 0.0;
         }
         ue0[i] = u[0]; ue1[i] = u[1]; ue2[i] = u[2];
-        uo0[i] = u[0]; uo1[i] = u[1]; uo2[i] = u[2];
+        if (SSM) {
+            if (!fixed)
+                for (int c = 0; c < 3; ++c) { su[0][c][i] = u[c]; su[1][c][i] = u[c]; }
+        } else {
+            uo0[i] = u[0]; uo1[i] = u[1]; uo2[i] = u[2];
+        }
         for (int r = 0; r < 3; ++r) {
             const double xv = dadd(Xv[r], u[r]);
             x0b[r * part_cap + k] = xv;
@@ -215,8 +238,15 @@ __device__ void solve_rve_fp64_cluster(cg::cluster_group &cl, Fp64ClusterShared 
     for (;;) {
         const int cb = (int)((it + 1) & 1);  // buffers of evaluation it + 1
         const int pb = cb ^ 1;               // ... and of evaluation it
-        double *const un0 = cb ? uo0 : ue0, *const un1 = cb ? uo1 : ue1, *const un2 = cb ? uo2 : ue2;
-        const double *const up0 = cb ? ue0 : uo0, *const up1 = cb ? ue1 : uo1, *const up2 = cb ? ue2 : uo2;
+        double *un0, *un1, *un2;
+        const double *up0, *up1, *up2;
+        if (SSM) {
+            un0 = cb ? su[1][0] : su[0][0]; un1 = cb ? su[1][1] : su[0][1]; un2 = cb ? su[1][2] : su[0][2];
+            up0 = cb ? su[0][0] : su[1][0]; up1 = cb ? su[0][1] : su[1][1]; up2 = cb ? su[0][2] : su[1][2];
+        } else {
+            un0 = cb ? uo0 : ue0; un1 = cb ? uo1 : ue1; un2 = cb ? uo2 : ue2;
+            up0 = cb ? ue0 : uo0; up1 = cb ? ue1 : uo1; up2 = cb ? ue2 : uo2;
+        }
         double *const xc = cb ? XB + 3 * part_cap : XB;
         // partial velocity update; update displacements (own free DOFs)
         for (int k = threadIdx.x; k < nfr; k += blockDim.x) {
@@ -332,7 +362,13 @@ __device__ void solve_rve_fp64_cluster(cg::cluster_group &cl, Fp64ClusterShared 
     double *xg = S.xg + 3 * n0;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int i = gidx(k);
-        if (fb == 1 && k < nfr) { ue0[i] = uo0[i]; ue1[i] = uo1[i]; ue2[i] = uo2[i]; }
+        if (SSM && k < nfr) {
+            ue0[i] = fb ? su[1][0][i] : su[0][0][i];
+            ue1[i] = fb ? su[1][1][i] : su[0][1][i];
+            ue2[i] = fb ? su[1][2][i] : su[0][2][i];
+        } else if (!SSM && fb == 1 && k < nfr) {
+            ue0[i] = uo0[i]; ue1[i] = uo1[i]; ue2[i] = uo2[i];
+        }
         xg[i] = xf[k];
         xg[n + i] = xf[part_cap + k];
         xg[2 * n + i] = xf[2 * part_cap + k];
@@ -352,14 +388,16 @@ __device__ void solve_rve_fp64_cluster(cg::cluster_group &cl, Fp64ClusterShared 
     cl.sync();  // the next RVE may overwrite the buffers
 }
 
-template <bool TSM>
+template <bool TSM, bool SSM>
 __global__ void __launch_bounds__(512, 1) dr_fp64_cluster_kernel(DevMesh M, DevState S, DevResults O,
-                                                                 SolveParams P, int part_cap, int slot_cap) {
+                                                                 SolveParams P, int part_cap, int free_cap,
+                                                                 int slot_cap) {
     extern __shared__ __align__(16) double dsm_fp64[];
     __shared__ Fp64ClusterShared sh;
     cg::cluster_group cl = cg::this_cluster();
-    double *XB = dsm_fp64;                  // [2][3][part_cap]
-    double *T = dsm_fp64 + 6 * part_cap;    // [3][slot_cap] when TSM
+    double *XB = dsm_fp64;                               // [2][3][part_cap]
+    double *ST = dsm_fp64 + 6 * part_cap;                // free-node state when SSM
+    double *T = ST + (SSM ? 13 * (size_t)free_cap : 0);  // [3][slot_cap] when TSM
     const int C = (int)cl.num_blocks();
     if ((int)threadIdx.x < C) {
         const int r = threadIdx.x;
@@ -373,15 +411,17 @@ __global__ void __launch_bounds__(512, 1) dr_fp64_cluster_kernel(DevMesh M, DevS
         const int item = *cl.map_shared_rank(&sh.item, 0);
         cl.sync();
         if (item >= P.queue_len) return;
-        solve_rve_fp64_cluster<TSM>(cl, sh, M, S, O, P, P.queue[item], XB, T, part_cap, slot_cap);
+        solve_rve_fp64_cluster<TSM, SSM>(cl, sh, M, S, O, P, P.queue[item], XB, ST, T, part_cap, free_cap,
+                                         slot_cap);
     }
 }
 
 namespace {
-using Fp64ClusterKernel = void (*)(DevMesh, DevState, DevResults, SolveParams, int, int);
+using Fp64ClusterKernel = void (*)(DevMesh, DevState, DevResults, SolveParams, int, int, int);
 
-Fp64ClusterKernel pick_fp64_cluster(bool tsm) {
-    return tsm ? dr_fp64_cluster_kernel<true> : dr_fp64_cluster_kernel<false>;
+Fp64ClusterKernel pick_fp64_cluster(bool tsm, bool ssm) {
+    if (tsm) return ssm ? dr_fp64_cluster_kernel<true, true> : dr_fp64_cluster_kernel<true, false>;
+    return ssm ? dr_fp64_cluster_kernel<false, true> : dr_fp64_cluster_kernel<false, false>;
 }
 
 cudaLaunchConfig_t fp64_cluster_config(int clusters, int parts, int block, size_t smem,
@@ -419,29 +459,31 @@ void prepare_fp64_cluster(Fp64ClusterKernel k, size_t smem) {
 }
 }  // namespace
 
-size_t fp64_cluster_smem(int part_cap, int slot_cap, bool tsm) {
-    return sizeof(double) * (6 * (size_t)part_cap + (tsm ? 3 * (size_t)slot_cap : 0));
+size_t fp64_cluster_smem(int part_cap, int free_cap, int slot_cap, bool tsm, bool ssm) {
+    return sizeof(double) * (6 * (size_t)part_cap + (ssm ? 13 * (size_t)free_cap : 0) +
+                             (tsm ? 3 * (size_t)slot_cap : 0));
 }
 
 int launch_dr_fp64_cluster(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
-                           int clusters, int parts, int block, int part_cap, int slot_cap, bool tsm,
-                           void *stream) {
+                           int clusters, int parts, int block, int part_cap, int free_cap, int slot_cap,
+                           bool tsm, bool ssm, void *stream) {
     cudaLaunchAttribute attr[1];
-    const size_t smem = fp64_cluster_smem(part_cap, slot_cap, tsm);
+    const size_t smem = fp64_cluster_smem(part_cap, free_cap, slot_cap, tsm, ssm);
     cudaLaunchConfig_t cfg = fp64_cluster_config(clusters, parts, block, smem, attr,
                                                  static_cast<cudaStream_t>(stream));
-    const Fp64ClusterKernel k = pick_fp64_cluster(tsm);
+    const Fp64ClusterKernel k = pick_fp64_cluster(tsm, ssm);
     prepare_fp64_cluster(k, smem);
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, m, s, r, p, part_cap, slot_cap);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, m, s, r, p, part_cap, free_cap, slot_cap);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }
 
-int occupancy_dr_fp64_cluster(int parts, int block, int part_cap, int slot_cap, bool tsm) {
+int occupancy_dr_fp64_cluster(int parts, int block, int part_cap, int free_cap, int slot_cap, bool tsm,
+                              bool ssm) {
     cudaLaunchAttribute attr[1];
-    const size_t smem = fp64_cluster_smem(part_cap, slot_cap, tsm);
+    const size_t smem = fp64_cluster_smem(part_cap, free_cap, slot_cap, tsm, ssm);
     cudaLaunchConfig_t cfg = fp64_cluster_config(parts * 64, parts, block, smem, attr, nullptr);
-    const Fp64ClusterKernel k = pick_fp64_cluster(tsm);
+    const Fp64ClusterKernel k = pick_fp64_cluster(tsm, ssm);
     prepare_fp64_cluster(k, smem);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {

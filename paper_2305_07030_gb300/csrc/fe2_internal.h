@@ -161,11 +161,14 @@ size_t mixed_lead_smem(int part_cap, int free_cap, int elem_cap, int slot_cap, s
 bool mixed_staged(int lead, size_t smem, int part_cap);
 // FP64 cluster kernel (dr_fp64_cluster.cu): dynamic shared memory (two
 // position buffers, and the element table when tsm), launch, occupancy.
-size_t fp64_cluster_smem(int part_cap, int slot_cap, bool tsm);
+// ssm: the own free nodes' state (displacement, velocity, acceleration, mass)
+// in shared memory as well.
+size_t fp64_cluster_smem(int part_cap, int free_cap, int slot_cap, bool tsm, bool ssm);
 int launch_dr_fp64_cluster(const DevMesh &m, const DevState &s, const DevResults &r, const SolveParams &p,
-                           int clusters, int parts, int block, int part_cap, int slot_cap, bool tsm,
-                           void *stream);
-int occupancy_dr_fp64_cluster(int parts, int block, int part_cap, int slot_cap, bool tsm);
+                           int clusters, int parts, int block, int part_cap, int free_cap, int slot_cap,
+                           bool tsm, bool ssm, void *stream);
+int occupancy_dr_fp64_cluster(int parts, int block, int part_cap, int free_cap, int slot_cap, bool tsm,
+                              bool ssm);
 // Shared memory per node of a kernel without its element table.
 size_t mixed_plain_node_bytes(int lead);
 // Resident CTAs per SM (FP64) / co-resident clusters (mixed) for a launch shape.

@@ -69,6 +69,7 @@ struct SizeClass {
     int smem_positions = 1;     // FP64: positions in shared memory
     bool fp64_cluster = false;  // FP64: one cluster of `parts` CTAs per RVE
     bool fp64_tsm = false;      // FP64 cluster: element table in shared memory
+    bool fp64_ssm = false;      // FP64 cluster: free-node state in shared memory
     int fslot_max = 0;          // FP64 cluster: most element slots of one part
     size_t smem_bytes = 0;      // dynamic shared memory per CTA
     int part_max = 0;           // mixed: largest part (nodes)
@@ -369,17 +370,29 @@ void build_classes(const std::vector<RveDesc> &rve, const std::vector<int32_t> &
         // FE2_FP64_CLUSTER=0 keeps every RVE on the single-CTA kernel.
         const bool clusters = env_int("FE2_FP64_CLUSTER", 1) != 0;
         auto on_cluster = [&](const RveDesc &R) {
-            return clusters && R.n_parts >= 2 && fp64_cluster_smem(R.part_max, 0, false) <= cap;
+            return clusters && R.n_parts >= 2 && fp64_cluster_smem(R.part_max, 0, 0, false, false) <= cap;
+        };
+        // shared-memory variant of an RVE: the element table first, then the
+        // free-node state, as far as they fit
+        auto variant = [&](int pm, int fm, int sm, bool &tsm, bool &ssm) {
+            const bool opts[4][2] = {{true, true}, {true, false}, {false, true}, {false, false}};
+            for (const auto &o : opts)
+                if (fp64_cluster_smem(pm, fm, sm, o[0], o[1]) <= cap) {
+                    tsm = o[0];
+                    ssm = o[1];
+                    return;
+                }
         };
         for (int32_t p : order) {
             const RveDesc &R = rve[p];
             if (!on_cluster(R)) continue;
-            const bool tsm = fp64_cluster_smem(R.part_max, R.part_fslot_max, true) <= cap;
+            bool tsm = false, ssm = false;
+            variant(R.part_max, part_free_max[p], R.part_fslot_max, tsm, ssm);
             SizeClass *c = nullptr;
             for (auto &k : out)
-                if (k.parts == R.n_parts && k.fp64_tsm == tsm &&
-                    (!tsm || fp64_cluster_smem(std::max(k.part_max, R.part_max),
-                                               std::max(k.fslot_max, R.part_fslot_max), true) <= cap)) {
+                if (k.parts == R.n_parts && k.fp64_tsm == tsm && k.fp64_ssm == ssm &&
+                    fp64_cluster_smem(std::max(k.part_max, R.part_max), std::max(k.free_max, part_free_max[p]),
+                                      std::max(k.fslot_max, R.part_fslot_max), tsm, ssm) <= cap) {
                     c = &k;
                     break;
                 }
@@ -389,12 +402,14 @@ void build_classes(const std::vector<RveDesc> &rve, const std::vector<int32_t> &
                 c->parts = R.n_parts;
                 c->fp64_cluster = true;
                 c->fp64_tsm = tsm;
+                c->fp64_ssm = ssm;
                 c->smem_positions = 0;
             }
             c->rves.push_back(p);
             c->part_max = std::max(c->part_max, R.part_max);
+            c->free_max = std::max(c->free_max, part_free_max[p]);
             c->fslot_max = std::max(c->fslot_max, R.part_fslot_max);
-            c->smem_bytes = fp64_cluster_smem(c->part_max, c->fslot_max, c->fp64_tsm);
+            c->smem_bytes = fp64_cluster_smem(c->part_max, c->free_max, c->fslot_max, c->fp64_tsm, c->fp64_ssm);
         }
         std::stable_sort(out.begin(), out.end(), [](const SizeClass &a, const SizeClass &b) {
             return a.parts > b.parts;
@@ -427,7 +442,18 @@ void build_classes(const std::vector<RveDesc> &rve, const std::vector<int32_t> &
                                                                              c.slot_max, limit), c.part_max);
             return l && f;
         };
-        for (int32_t p : order) {
+        // first-fit decreasing: the RVEs with the largest shared-memory needs
+        // open the classes, so that smaller ones fit under their maxima (the
+        // queue order inside a class is restored to LPT afterwards)
+        std::vector<size_t> need(rve.size(), 0);
+        for (int32_t p : order)
+            need[p] = mixed_fp32_smem(rve[p].part_max, part_free_max[p], rve[p].part_elem_max,
+                                      rve[p].part_slot_max, (size_t)1 << 40);
+        std::vector<int32_t> ffd = order;
+        std::stable_sort(ffd.begin(), ffd.end(), [&](int32_t x, int32_t y) { return need[x] > need[y]; });
+        std::vector<int32_t> rank(rve.size(), 0);
+        for (size_t k = 0; k < order.size(); ++k) rank[order[k]] = (int32_t)k;
+        for (int32_t p : ffd) {
             const RveDesc &R = rve[p];
             SizeClass one;
             one.parts = R.n_parts;
@@ -463,6 +489,8 @@ void build_classes(const std::vector<RveDesc> &rve, const std::vector<int32_t> &
                 out.push_back(std::move(one));
             }
         }
+        for (auto &c : out)
+            std::stable_sort(c.rves.begin(), c.rves.end(), [&](int32_t x, int32_t y) { return rank[x] < rank[y]; });
         // the class holding the largest RVEs (longest critical path) first
         std::stable_sort(out.begin(), out.end(), [](const SizeClass &a, const SizeClass &b) {
             return a.parts > b.parts;
@@ -928,7 +956,10 @@ extern "C" fe2_status fe2_batch_create(int32_t n_rve, const int64_t *node_off, c
         A(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming), "done event");
         A(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "capture stream");
     }
-    for (int k = 0; k < 8 && rc == FE2_OK; ++k) {
+    // one stream per launch class (at least 8), so that classes never queue
+    // behind each other
+    const size_t n_side = std::max<size_t>(8, std::max(b->classes_fp64.size(), b->classes_mixed.size()));
+    for (size_t k = 0; k < n_side && rc == FE2_OK; ++k) {
         cudaStream_t s;
         A(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
         if (rc == FE2_OK) b->side.push_back(s);
@@ -1098,17 +1129,22 @@ int resident_of(fe2_batch *b, int kind, int parts, int block, size_t smem, int p
     const auto key = std::make_tuple(kind, parts, block, smem, part_cap);
     auto it = b->occ.find(key);
     if (it != b->occ.end()) return it->second;
-    // kind: 0/1 mixed FP32/lead, 2 FP64 single CTA (parts = positions staged),
-    // 3 FP64 cluster (smem encodes the table choice through its size)
-    int r;
-    if (kind == 3) {
-        const size_t plain = fp64_cluster_smem(part_cap, 0, false);
-        const int slots = smem > plain ? (int)((smem - plain) / (3 * sizeof(double))) : 0;
-        r = occupancy_dr_fp64_cluster(parts, block, part_cap, slots, smem > plain);
-    } else {
-        r = kind == 2 ? occupancy_dr_fp64(parts, block, smem)
-                      : occupancy_dr_mixed(kind, parts, block, smem, part_cap);
-    }
+    // kind: 0/1 mixed FP32/lead, 2 FP64 single CTA (parts = positions staged)
+    const int r = kind == 2 ? occupancy_dr_fp64(parts, block, smem)
+                            : occupancy_dr_mixed(kind, parts, block, smem, part_cap);
+    b->occ[key] = r;
+    return r;
+}
+
+// Resident clusters of an FP64 cluster class (cached like resident_of; the
+// key's kind 3 + 2 tsm + ssm and the smem size identify the variant).
+int resident_fp64_cluster(fe2_batch *b, const SizeClass &c, int block) {
+    const auto key = std::make_tuple(3 + 2 * (int)c.fp64_tsm + (int)c.fp64_ssm, c.parts, block, c.smem_bytes,
+                                     c.part_max);
+    auto it = b->occ.find(key);
+    if (it != b->occ.end()) return it->second;
+    const int r = occupancy_dr_fp64_cluster(c.parts, block, c.part_max, c.free_max, c.fslot_max, c.fp64_tsm,
+                                            c.fp64_ssm);
     b->occ[key] = r;
     return r;
 }
@@ -1131,7 +1167,7 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
     P.smem_positions = c.smem_positions;
     if (fp64 && c.fp64_cluster) {
         const int block = o.block_threads ? o.block_threads : 512;
-        const int resident = resident_of(b, 3, c.parts, block, c.smem_bytes, c.part_max);
+        const int resident = resident_fp64_cluster(b, c, block);
         if (resident < 1)
             return fail(FE2_ECUDA, "no FP64 cluster of " + std::to_string(c.parts) + " CTAs fits");
         if (timed) {
@@ -1139,7 +1175,7 @@ fe2_status launch_class(fe2_batch *b, const fe2_opts &o, const SizeClass &c, Sol
             CUDA_TRY(record_timing(b->tev[*timed], s, capturing));
         }
         const int e = launch_dr_fp64_cluster(M, S, R, P, std::min(nq, resident), c.parts, block, c.part_max,
-                                             c.fslot_max, c.fp64_tsm, s);
+                                             c.free_max, c.fslot_max, c.fp64_tsm, c.fp64_ssm, s);
         if (e != 0) return fail(FE2_ECUDA, std::string("launch: ") + cudaGetErrorString((cudaError_t)e));
         if (timed) {
             CUDA_TRY(record_timing(b->tev[*timed + 1], s, capturing));
@@ -1255,7 +1291,7 @@ fe2_status warm_shapes(fe2_batch *b, const fe2_opts &o) {
     for (const SizeClass &c : fp64 ? b->classes_fp64 : b->classes_mixed) {
         if (fp64 && c.fp64_cluster) {
             const int block = o.block_threads ? o.block_threads : 512;
-            if (resident_of(b, 3, c.parts, block, c.smem_bytes, c.part_max) < 1)
+            if (resident_fp64_cluster(b, c, block) < 1)
                 return fail(FE2_ECUDA, "no FP64 cluster of " + std::to_string(c.parts) + " CTAs fits");
             continue;
         }

@@ -75,9 +75,10 @@ def test_fp64_cluster_kernel_bitwise_trajectory(max_iter):
     """RVEs of several parts run the FP64 cluster kernel (one part per CTA,
     neighbours through distributed shared memory, element slots per part):
     the trajectory is still the oracle's bit for bit, at a fixed iteration
-    cap (2, 4, 8 and 16 parts, the largest with its element table in global
-    memory) and to convergence."""
-    sizes = [1500, 3000, 6000, 40000] if max_iter == 400 else [1300, 2600]
+    cap (2 to 16 parts; small parts keep the element table and the free-node
+    state in shared memory, the 40,000-node RVE's parts neither) and to
+    convergence."""
+    sizes = [1500, 3000, 6000, 20000, 40000] if max_iter == 400 else [1300, 2600]
     w = _workload(sizes, seed=15)
     from paper_2305_07030_gb300 import plan
     assert sorted(set(int(x) for x in plan(w.nets)["parts"])) == \
