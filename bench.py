@@ -624,7 +624,7 @@ def main():
     ap.add_argument("--rves", default="", help="comma-separated RVE subset (profiling runs)")
     ap.add_argument("--max-iter", type=int, default=10_000_000)
     ap.add_argument("--lead-iters", type=int, default=-1)
-    ap.add_argument("--lead-tol", type=float, default=1e-3,
+    ap.add_argument("--lead-tol", type=float, default=1e-2,
                     help="mixed: relative residual that ends the double-float lead")
     ap.add_argument("--block", type=int, default=0, help="threads per CTA (0 = library default)")
     ap.add_argument("--launch", default="graph", choices=["graph", "stream"],

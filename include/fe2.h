@@ -114,7 +114,7 @@ typedef struct {
                              captured by the first solve with this option
                              set (default); 1 = plain stream launches */
     double lead_tol;      /* MIXED: relative residual that ends the lead
-                             phase (default 1e-3) */
+                             phase (default 1e-2) */
     int64_t stall_window; /* MIXED: FP32 evaluations in which the squared
                              residual must fall to a quarter of its reference
                              value; when it does not (the FP32 increments have

@@ -210,7 +210,7 @@ _INIT = {"reference": 0, "affine": 1, "warm": 2}
 
 def make_opts(tol=1e-8, max_iter=10_000_000, dt_safety=0.9, precision="mixed", init="affine",
               kinetic_energy=False, block_threads=0, lead_iters=-1, rebase_every=0,
-              lead_tol=1e-3, launch="graph", stall_window=0) -> Opts:
+              lead_tol=1e-2, launch="graph", stall_window=0) -> Opts:
     o = Opts()
     _lib.fe2_opts_default(C.byref(o))
     o.tol = float(tol)

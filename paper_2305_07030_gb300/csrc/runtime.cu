@@ -290,7 +290,7 @@ void fe2_opts_default(fe2_opts *o) {
     o->block_threads = 0;
     o->lead_iters = -1;
     o->rebase_every = 0;
-    o->lead_tol = 1e-3;
+    o->lead_tol = 1e-2;
     o->stall_window = 0;
 }
 

@@ -35,7 +35,7 @@ def test_opts_defaults():
     o = m.make_opts()
     assert o.tol == 1e-8 and o.max_iter == 10_000_000 and o.dt_safety == 0.9
     assert o.precision == 1 and o.init == 1 and o.lead_iters == -1
-    assert C.sizeof(m.Opts) == 72 and o.lead_tol == 1e-3
+    assert C.sizeof(m.Opts) == 72 and o.lead_tol == 1e-2
     assert o.launch == 0 and o.stall_window == 0
 
 

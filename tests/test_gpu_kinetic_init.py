@@ -77,7 +77,7 @@ def test_kinetic_energy_mixed_lead_and_fp32_phase():
     """Mixed: all iterations in the double-float lead, then all in FP32."""
     for w in (_chain(), _workload([150, 400], seed=42)):
         ref = _oracle_ke(w, max_iter=60)
-        out = _ke(w, precision="mixed", max_iter=60)  # 60 lead iterations
+        out = _ke(w, precision="mixed", max_iter=60, lead_tol=0.0)  # 60 lead iterations
         for p, r in enumerate(ref):
             assert out["iters"][p] == 60 and out["status"][p] == "MAXITER"
             assert abs(out["ke"][p] - r["ke"]) <= 1e-5 * r["ke"], (p, out["ke"][p], r["ke"])
