@@ -368,7 +368,8 @@ def run_ours(args, rank, world):
     }
     if args.dump:
         np.savez(args.dump, sigma=sigma, iters=iters, status=status, n_nodes=nn,
-                 lead=np.asarray(leads))
+                 lead=np.asarray(leads), kernel_ms=np.asarray(kernel_ms[-1]),
+                 rve_class=(fe2.plan(nets)["rve_class"] if mixed else np.zeros(P, np.int32)))
     if mixed and args.workload == "rve5000x64" and not args.no_naive:
         nv = naive_comparator(w, iters)
         nv["speedup_of_batched"] = value / nv["solves_per_s"]

@@ -68,7 +68,11 @@ typedef enum {
      * in the same order as a serial element-scatter implementation in the
      * caller's node order, no fused multiply-add, correctly rounded sqrt and
      * divide. The trajectory is bit for bit that of such an implementation;
-     * only the residual and stress sums are reassociated. One CTA per RVE. */
+     * only the residual and stress sums are reassociated. An RVE of one
+     * spatial part runs on one CTA; an RVE of several parts on a
+     * thread-block cluster, one part per CTA, with the same operations (set
+     * FE2_FP64_CLUSTER=0 in the environment before fe2_batch_create to keep
+     * every RVE on one CTA). Any RVE size. */
     FE2_PREC_FP64 = 0,
     /* All iteration arithmetic on the FP32 pipes, one thread-block cluster
      * of 1-16 CTAs per RVE: a double-float (FP32 pair) lead phase until the
