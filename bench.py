@@ -510,7 +510,9 @@ def run_serving(args):
     with fe2.Batch(nets, damping=damping) as b:
         t0 = time.perf_counter()
         out = b.serve(rve, t_arr, F, max_batch=args.serve_batch,
-                      max_inflight_bytes=args.serve_inflight_gb * 1e9)
+                      max_inflight_bytes=args.serve_inflight_gb * 1e9,
+                      first=dict(max_iter=args.max_iter),
+                      next=dict(max_iter=args.max_iter, init="warm"))
         wall = time.perf_counter() - t0
     lat = out["t_done"] - t_arr
     return {"metric": "serving p99 latency", "value": float(np.percentile(lat, 99)), "unit": "s",
@@ -520,7 +522,8 @@ def run_serving(args):
                                    f"log-U({args.serve_lo},{args.serve_hi}), Poisson arrivals "
                                    f"{args.serve_rate}/s, F=diag(1+0.005k,1,1)(I+0.02 S), warm "
                                    f"restarts, micro-batches <= {args.serve_batch}, in-flight "
-                                   f"budget {args.serve_inflight_gb or 'none'} GB"},
+                                   f"budget {args.serve_inflight_gb or 'none'} GB, max_iter "
+                                   f"{args.max_iter}"},
             "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)),
             "latency_max_s": float(lat.max()),
