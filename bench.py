@@ -217,6 +217,12 @@ def run_ours(args, rank, world):
     nets = w.nets
     P = len(nets)
     mixed = args.precision == "mixed"
+    if args.autotune and mixed:
+        # tune the cluster and CTA sizes per size bucket on up to 16 RVEs
+        # spread over the sizes, before the batch is created
+        pick = ri.stratified_idx([n.n_nodes for n in nets], min(16, P))
+        sub = w.subset(pick)
+        fe2.autotune(sub.nets, sub.F, sub.damping, trial_iters=args.autotune_iters)
     batch = fe2.Batch(nets, damping=w.damping)
     opts = dict(precision=args.precision, init="affine", tol=1e-8, max_iter=args.max_iter,
                 lead_iters=args.lead_iters, lead_tol=args.lead_tol, block_threads=args.block,
@@ -635,6 +641,9 @@ def main():
                     help="replay the solve as a CUDA graph (default) or launch on streams")
     ap.add_argument("--tuning", default="", help="JSON file written by fe2_autotune to load first")
     ap.add_argument("--dump", default="", help="write the per-RVE results (npz) to this path")
+    ap.add_argument("--autotune", action="store_true",
+                    help="mixed: run fe2_autotune on a size-stratified sample first")
+    ap.add_argument("--autotune-iters", type=int, default=2000)
     ap.add_argument("--tune", default="",
                     help="explicit tuning: bucket:parts:block_fp32[:block_lead],... (2^bucket <= nodes)")
     ap.add_argument("--serve", action="store_true", help="run the serving scenario instead")
