@@ -1,6 +1,6 @@
 """Parity helpers shared by the GPU tests (test-only; uses the oracle).
 
-Mixed-precision results are held to the benchmark spec's bound of 1e-5 relative
+Mixed-precision results are held to the target bound of 1e-5 relative
 stress error against the FP64 oracle wherever the oracle itself determines
 the stress to that level. Random kNN fiber networks (mean degree about 5,
 below the 6 of a rigid 3-D truss) carry floppy modes that only pre-stress
@@ -144,7 +144,7 @@ def within_family(net, F, c, sigma, base_sigma, diameter, tol=1e-8, alpha=0.9, i
         runs += list(ex.map(ea_ulps, range(EA_SEEDS)))
     ext = mixed_bound(family_diameter([np.asarray(base_sigma)] + runs, base_sigma))
     # inside the extended family's spread, or on one of its members' equilibria
-    # (within the benchmark spec's tolerance of a member, relative to the base stress)
+    # (within the 1e-5 target tolerance of a member, relative to the base stress)
     nb = np.linalg.norm(np.asarray(base_sigma))
     nearest = min(np.linalg.norm(np.asarray(sigma) - r) / nb for r in runs)
     return err <= ext or nearest <= MIXED_TOL, err, ext

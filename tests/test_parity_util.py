@@ -26,7 +26,7 @@ def test_family_diameter_is_largest_pairwise_distance():
     assert family_diameter([base], base) == 0.0
 
 
-def test_mixed_bound_floor_is_the_north_star_tolerance():
+def test_mixed_bound_floor_is_the_stated_tolerance():
     assert mixed_bound(0.0) == 1e-5 and mixed_bound(3e-6) == 1e-5
     assert mixed_bound(4e-4) == 4e-4
 
