@@ -79,3 +79,24 @@ def test_mixed_path_size_limit():
         P = m.plan([ri.random_network(n, np.random.default_rng(43))], smem_optin=SMEM_OPTIN)
         assert list(P["parts"]) == [16]
         assert bool((P["smem"] <= budget).all()) == fits, (n, P["smem"].tolist())
+
+
+def test_plan_of_an_uneven_batch_with_many_classes():
+    """The 64 size-stratified RVEs of the 4096 x log-U(500, 20k) workload
+    split into more than eight launch classes (cluster size and staging per
+    RVE); every RVE is in exactly one class, every class fits, and an RVE's
+    class key does not depend on the batch it is in."""
+    import paper_2305_07030_gb300 as m
+    idx = ri.stratified_idx(ri.uneven_sizes(4096, 500, 20000, 4), 64)
+    w = ri.uneven_subset(4096, 500, 20000, 4, idx)
+    P = m.plan(w.nets, smem_optin=SMEM_OPTIN)
+    k = P["n_classes"]
+    assert k > 8 and len(P["parts"]) == k
+    assert int(P["rves"].sum()) == 64
+    assert np.array_equal(np.bincount(P["rve_class"], minlength=k), P["rves"])
+    assert (P["smem"] <= SMEM_OPTIN - 16384).all()
+    for p in (0, 31, 63):
+        alone = m.plan([w.nets[p]], smem_optin=SMEM_OPTIN)
+        c = P["rve_class"][p]
+        assert (int(alone["parts"][0]), *map(int, alone["staged"][0])) == \
+            (int(P["parts"][c]), *map(int, P["staged"][c]))
