@@ -27,6 +27,11 @@ MUTATIONS = {
                             "if (fixed[i]) u[3 * i + r] = uaff;"),
     "kinetic energy without mass": ("ke += 0.5 * m[i] * (v[3 * i] * v[3 * i]",
                                     "ke += 0.5 * (v[3 * i] * v[3 * i]"),
+    "internal work without the previous force": ("wi += du * (gp[3 * i + r] + g[3 * i + r]);",
+                                                   "wi += du * (2.0 * g[3 * i + r]);"),
+    "internal work sign": ("wint -= 0.5 * wi;", "wint += 0.5 * wi;"),
+    "damping work half-step": ("double du = dt * v[3 * i + r];", "double du = 0.5 * dt * v[3 * i + r];"),
+    "damping work previous force kept": ("fdp[3 * i + r] = fd;", "fdp[3 * i + r] = 0.0;"),
     "residual over all nodes": ("if (fixed[i]) continue;\n            for (int r = 0; r < 3; ++r) {\n                double fd",
                                 "for (int r = 0; r < 3; ++r) {\n                double fd"),
 }
