@@ -239,6 +239,30 @@ fe2_status fe2_batch_layout(int32_t n_rve, const int64_t *node_off, const double
                             int32_t *col_part, int32_t *part_off);
 
 /*
+ * Inspection call, host only: the element slot tables of the FP64 cluster
+ * kernel for these inputs (Algorithm 1, getInternalForces on a cluster: each
+ * CTA evaluates the elements with an end among its part's free nodes once per
+ * iteration). Inputs as for fe2_batch_layout. Outputs (HOST, caller-allocated,
+ * each may be NULL):
+ * n_slots    total slots of the batch.
+ * slot0      n_rve: the RVE's first slot.
+ * part_slot  n_rve * 17: per RVE the parts' first slots relative to slot0
+ *            (entry r+1 ends part r; entries past the RVE's parts repeat).
+ * slot       4 per slot, at most cap slots: RVE-local element (caller
+ *            numbering), its first and its second end as (part << 16 |
+ *            index in the part's node order), 0.
+ * csr_slot   2*E: per CSR entry (fe2_batch_layout's order) of a free node,
+ *            its slot relative to its part's first << 1, | 1 when the node
+ *            is the element's second end; -1 for entries of fixed nodes.
+ * Returns FE2_EINVAL for the inputs fe2_batch_layout rejects.
+ */
+fe2_status fe2_batch_fp64_slots(int32_t n_rve, const int64_t *node_off, const double *X,
+                                const int64_t *elem_off, const int32_t *conn, const double *EA,
+                                const uint8_t *fixed, int64_t smem_optin, int32_t nodes_per_cta,
+                                int64_t cap, int64_t *n_slots, int64_t *slot0, int32_t *part_slot,
+                                int32_t *slot, int32_t *csr_slot);
+
+/*
  * Inspection call, host only: the launch plan of the mixed solver
  * (FE2_PREC_MIXED) for these inputs, with the default CTA size. RVEs are
  * grouped into classes by cluster size; each class runs two persistent

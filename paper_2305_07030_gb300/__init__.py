@@ -86,6 +86,7 @@ def _load():
     lib.fe2_autotune.argtypes = [I32, P, P, P, P, P, P, P, P, I64, C.c_char_p, C.POINTER(Tuning)]
     lib.fe2_shard_plan.argtypes = [I32, P, P, I32, P, P]
     lib.fe2_batch_energy.argtypes = [P, P, P, P, P]
+    lib.fe2_batch_fp64_slots.argtypes = [I32, P, P, P, P, P, P, I64, I32, I64, P, P, P, P, P]
     lib.fe2_last_error.argtypes = []
     lib.fe2_last_error.restype = C.c_char_p
     for name in ("fe2_batch_create", "fe2_batch_solve", "fe2_batch_solve_dev",
@@ -95,7 +96,7 @@ def _load():
                  "fe2_batch_diagnostics", "fe2_batch_parts", "fe2_batch_submit",
                  "fe2_batch_poll", "fe2_serve", "fe2_batch_layout", "fe2_batch_plan",
                  "fe2_tuning_set", "fe2_tuning_get", "fe2_tuning_load", "fe2_autotune",
-                 "fe2_shard_plan", "fe2_batch_energy"):
+                 "fe2_shard_plan", "fe2_batch_energy", "fe2_batch_fp64_slots"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -301,6 +302,26 @@ def plan(nets, smem_optin=232448, nodes_per_cta=0):
         out[key] = out[key][:k]
     for key in ("smem", "staged", "block"):
         out[key] = out[key][:2 * k].reshape(k, 2)  # columns: lead, FP32
+    return out
+
+
+def fp64_slots(nets, smem_optin=232448, nodes_per_cta=0):
+    """The FP64 cluster kernel's element slot tables for ``Batch(nets)``,
+    computed on the host (``fe2_batch_fp64_slots``)."""
+    n_rve = len(nets)
+    node_off, X, elem_off, conn, EA, fixed = _pack_inputs(nets)
+    E = int(elem_off[-1])
+    ns = C.c_int64()
+    args = (n_rve, _ptr(node_off), _ptr(X), _ptr(elem_off), _ptr(conn), _ptr(EA), _ptr(fixed),
+            int(smem_optin), int(nodes_per_cta))
+    _check(_lib.fe2_batch_fp64_slots(*args, 0, C.byref(ns), None, None, None, None))
+    out = {"slot0": np.zeros(n_rve, np.int64), "part_slot": np.zeros(n_rve * 17, np.int32),
+           "slot": np.zeros(4 * max(1, ns.value), np.int32), "csr_slot": np.zeros(2 * E, np.int32)}
+    _check(_lib.fe2_batch_fp64_slots(*args, ns.value, C.byref(ns), _ptr(out["slot0"]),
+                                     _ptr(out["part_slot"]), _ptr(out["slot"]), _ptr(out["csr_slot"])))
+    out["n_slots"] = ns.value
+    out["part_slot"] = out["part_slot"].reshape(n_rve, 17)
+    out["slot"] = out["slot"][:4 * ns.value].reshape(-1, 4)
     return out
 
 

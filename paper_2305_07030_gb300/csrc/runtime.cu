@@ -1033,6 +1033,28 @@ extern "C" fe2_status fe2_batch_layout(int32_t n_rve, const int64_t *node_off, c
     return FE2_OK;
 }
 
+extern "C" fe2_status fe2_batch_fp64_slots(int32_t n_rve, const int64_t *node_off, const double *X,
+                                           const int64_t *elem_off, const int32_t *conn, const double *EA,
+                                           const uint8_t *fixed, int64_t smem_optin, int32_t nodes_per_cta,
+                                           int64_t cap, int64_t *n_slots, int64_t *slot0, int32_t *part_slot,
+                                           int32_t *slot, int32_t *csr_slot) {
+    const fe2_status v = validate_batch(n_rve, node_off, X, elem_off, conn, EA, fixed, nullptr, nullptr);
+    if (v != FE2_OK) return v;
+    if (smem_optin <= 16384) return fail(FE2_EINVAL, "smem_optin must exceed 16384 bytes");
+    const int target = std::max(64, nodes_per_cta > 0 ? nodes_per_cta : env_int("FE2_NODES_PER_CTA", 1024));
+    HostLayout L;
+    build_layout(n_rve, node_off, X, elem_off, conn, EA, fixed, nullptr, nullptr, target,
+                 (size_t)smem_optin - 16384, L);
+    const int64_t ns = (int64_t)(L.fpSlot.size() / 4);
+    if (n_slots) *n_slots = ns;
+    if (slot0)
+        for (int32_t p = 0; p < n_rve; ++p) slot0[p] = L.rve[p].slot0;
+    if (part_slot) std::copy(L.fpPartSlot.begin(), L.fpPartSlot.end(), part_slot);
+    if (slot) std::copy(L.fpSlot.begin(), L.fpSlot.begin() + 4 * std::min(ns, std::max<int64_t>(cap, 0)), slot);
+    if (csr_slot) std::copy(L.fpCsrSlot.begin(), L.fpCsrSlot.end(), csr_slot);
+    return FE2_OK;
+}
+
 extern "C" fe2_status fe2_batch_plan(int32_t n_rve, const int64_t *node_off, const double *X,
                                      const int64_t *elem_off, const int32_t *conn, const double *EA,
                                      const uint8_t *fixed, int64_t smem_optin, int32_t nodes_per_cta,

@@ -159,3 +159,53 @@ def test_rejects_tiny_shared_memory():
     import paper_2305_07030_gb300 as m
     with pytest.raises(m.FE2Error, match="smem_optin"):
         m.layout(_nets([50], seed=34), smem_optin=4096)
+
+
+def test_fp64_cluster_slot_tables():
+    """The FP64 cluster kernel's element slots (fe2_batch_fp64_slots): per
+    part one slot per element with an end among the part's free nodes, each
+    once; every CSR entry of a free node points at the slot of its own
+    element in its own part, with the orientation bit set exactly when the
+    node is the element's second end in the caller's numbering; the slot's
+    ends carry the (part << 16 | index) of col_part."""
+    import paper_2305_07030_gb300 as m
+    rng = np.random.default_rng(71)
+    nets = [ri.random_network(int(n), rng) for n in (300, 1700, 4100)]
+    L = m.layout(nets, smem_optin=SMEM_OPTIN)
+    T = m.fp64_slots(nets, smem_optin=SMEM_OPTIN)
+    slots, csr = T["slot"], T["csr_slot"]
+    assert T["n_slots"] == len(slots) and T["slot0"][0] == 0
+    for p, net in enumerate(nets):
+        n0, e0 = int(L["node_off"][p]), int(L["elem_off"][p])
+        C = int(L["parts"][p])
+        pf = L["part_off"][p, 0]
+        ps = T["part_slot"][p]
+        base = int(T["slot0"][p])
+        perm = L["perm"][n0:n0 + net.n_nodes] - n0          # permuted -> caller id
+        rp = L["rowptr"][n0 + p:n0 + p + net.n_nodes + 1]
+        csr0 = 2 * e0
+        edge = {}
+        for e, (a, b) in enumerate(net.elems):
+            edge[(int(a), int(b))] = edge[(int(b), int(a))] = e
+        for r in range(C):
+            own = slots[base + ps[r]:base + ps[r + 1]]
+            assert len(set(own[:, 0].tolist())) == len(own)  # each element once per part
+            used = set()
+            for k in range(pf[r], pf[r + 1]):                # the part's free nodes
+                i = int(perm[k])
+                for q in range(rp[k], rp[k + 1]):
+                    w = int(csr[csr0 + q])
+                    assert w >= 0
+                    sl = own[w >> 1]
+                    j = int(perm[L["col"][csr0 + q]])
+                    e = edge[(i, j)]
+                    assert sl[0] == e
+                    a, b = (int(x) for x in net.elems[e])
+                    assert (w & 1) == (1 if i == b else 0)
+                    # the far end's (part, index) matches col_part of this entry
+                    far = sl[2] if i == a else sl[1]
+                    assert far == L["col_part"][csr0 + q]
+                    used.add(w >> 1)
+            assert used == set(range(len(own)))              # no slot unused
+        for r in range(C, 16):
+            assert ps[r + 1] == ps[C]
