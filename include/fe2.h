@@ -265,8 +265,10 @@ fe2_status fe2_batch_fp64_slots(int32_t n_rve, const int64_t *node_off, const do
 /*
  * Inspection call, host only: the launch plan of the mixed solver
  * (FE2_PREC_MIXED) for these inputs, with the default CTA size. RVEs are
- * grouped into classes by cluster size; each class runs two persistent
- * launches (Algorithm 1's loop: the double-float lead, then the FP32 phase).
+ * grouped into classes by cluster size and element-table staging; each class
+ * runs three persistent launches (Algorithm 1's loop: the double-float lead,
+ * the FP32 phase, and the double-float resume of RVEs whose FP32 residual
+ * stalled) on a stream of its own.
  *
  * Inputs as for fe2_batch_layout. Outputs (HOST, caller-allocated; each may
  * be NULL); classes beyond max_classes are counted but not written:
@@ -298,9 +300,11 @@ fe2_status fe2_batch_plan(int32_t n_rve, const int64_t *node_off, const double *
  *       `stream` before the call returns).
  * opts  solver options, or NULL for fe2_opts_default().
  *
- * All RVEs run in one persistent launch per size class; the host returns as
- * soon as the work is queued. Results are read with fe2_batch_stress() or
- * fe2_batch_results_dev().
+ * The RVEs run in persistent launches per size class (one for FP64; lead,
+ * FP32 phase and resume for MIXED), the classes concurrently; the first solve
+ * with an option set records them into a CUDA graph that later solves
+ * replay (opts.launch). The host returns as soon as the work is queued.
+ * Results are read with fe2_batch_stress() or fe2_batch_results_dev().
  */
 fe2_status fe2_batch_solve(fe2_batch *b, const double *F, const fe2_opts *opts, void *stream);
 

@@ -1,5 +1,6 @@
 // Mixed-precision dynamic relaxation (Algorithm 1) for a batch of RVEs: one
-// thread-block cluster per RVE, two persistent launches per size class.
+// thread-block cluster per RVE, three persistent launches per size class (the
+// double-float lead, the FP32 phase, the double-float resume of stalled RVEs).
 //
 // Layout. The RVE is split spatially into `parts` pieces, one per CTA of the
 // cluster; a CTA stages the state of its own nodes in its shared memory and
